@@ -1,0 +1,235 @@
+"""Pins of the oracle's storage codecs against what the paper and mathematics fix.
+
+Each test checks the oracle (oracle/codecs.cpp) against something other than
+itself: bit patterns printed in Fig. 2, properties printed in Table 2, accuracy
+intervals stated in Sec. 3.2.2, numpy's IEEE binary16 conversion, the prose
+FP16C algorithm of Sec. 3.1.4, and brute-force nearest-value search over the
+decoded code table.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import golden
+
+ALL_MAG = np.arange(0x8000, dtype=np.uint16)
+
+
+def table(fmt):
+    """Decoded magnitudes of codes 0..0x7FFF as float64."""
+    return oracle.decode(fmt, ALL_MAG).astype(np.float64)
+
+
+@pytest.mark.parametrize("row", golden("one_fig2.txt"), ids=lambda r: r[0])
+def test_fig2_bit_pattern_of_one(row):
+    fmt, bits = row[0], "".join(row[1:])
+    assert len(bits) == 16
+    code = int(bits, 2)
+    assert int(oracle.encode(fmt, [1.0])[0]) == code
+    assert oracle.decode(fmt, [code])[0] == 1.0
+
+
+@pytest.mark.parametrize("row", golden("format_table2.txt"), ids=lambda r: r[0])
+def test_table2_range_and_smallest_numbers(row):
+    fmt, eps, rng, min_norm, min_den = row
+    t = table(fmt)
+    finite = t[np.isfinite(t)]
+    assert np.isclose(finite.max(), float(rng), rtol=6e-7)
+    assert np.isclose(finite[finite > 0].min(), float(min_den), rtol=6e-7)
+    if min_norm != "-":
+        first_normal = {"FP16": 0x0400, "FP16S": 0x0400, "FP16C": 0x0800}[fmt]
+        assert np.isclose(t[first_normal], float(min_norm), rtol=6e-7)
+    # epsilon: value spacing relative to the start of a binade, at its best
+    pos = np.unique(finite[finite > 0])
+    rel = np.diff(pos) / pos[:-1]
+    rel = rel[np.log2(pos[:-1]) == np.round(np.log2(pos[:-1]))]
+    assert float(f"{rel.min():.1e}") == pytest.approx(float(eps), rel=1e-9)
+
+
+@pytest.mark.parametrize("fmt", oracle.CODEC_FORMATS)
+def test_decode_is_monotone_and_sign_magnitude(fmt):
+    t = table(fmt)
+    fin = np.isfinite(t)
+    d = np.diff(t[fin])
+    assert np.all(d >= 0)
+    ties = np.flatnonzero(d == 0)
+    if fmt == "P16_2C":
+        # the one documented reading: with 13 regime zeros the exponent bit
+        # that still fits is read as zero, so codes 2 and 3 share a value
+        assert ties.tolist() == [2]  # the pair of codes (2, 3)
+    else:
+        assert ties.size == 0
+    neg = oracle.decode(fmt, ALL_MAG | 0x8000).astype(np.float64)
+    assert np.array_equal(neg[fin], -t[fin])
+
+
+@pytest.mark.parametrize("fmt", oracle.CODEC_FORMATS)
+def test_encode_decode_round_trip(fmt):
+    codes = np.arange(0x10000, dtype=np.uint16)
+    vals = oracle.decode(fmt, codes)
+    keep = ~np.isnan(vals)
+    back = oracle.encode(fmt, vals)
+    bad = np.flatnonzero(keep & (back != codes))
+    if fmt == "P16_2C":
+        # 2^-59 (code 1) lies below the encoder's flush threshold and 2^-55
+        # is produced as code 3: the two codes the encoder never emits
+        assert sorted(set((codes[bad] & 0x7FFF).tolist())) == [1, 2]
+    else:
+        assert bad.size == 0, [hex(c) for c in codes[bad][:8]]
+
+
+def _interesting_floats(rng, lo_exp, hi_exp, n=200000):
+    mags = np.exp2(rng.uniform(lo_exp, hi_exp, n)).astype(np.float32)
+    signs = np.where(rng.uniform(size=n) < 0.5, -1.0, 1.0).astype(np.float32)
+    return mags * signs
+
+
+def test_fp16_matches_numpy_binary16():
+    rng = np.random.default_rng(7)
+    x = np.concatenate([
+        _interesting_floats(rng, -30, 17),
+        np.arange(0x10000, dtype=np.uint16).view(np.float16).astype(np.float32),
+    ])
+    # exact midpoints between neighbouring binary16 values: ties-to-even
+    h = np.arange(0x7BFF, dtype=np.uint16).view(np.float16).astype(np.float64)
+    mids = ((h[:-1] + h[1:]) / 2).astype(np.float32)
+    x = np.concatenate([x, mids, -mids])
+    x = x[~np.isnan(x)]
+    with np.errstate(over="ignore"):
+        ref = x.astype(np.float16).view(np.uint16)
+    assert np.array_equal(oracle.encode("FP16", x), ref)
+    with np.errstate(over="ignore"):
+        ref_s = (x * np.float32(32768.0)).astype(np.float16).view(np.uint16)
+    assert np.array_equal(oracle.encode("FP16S", x), ref_s)
+    codes = np.arange(0x10000, dtype=np.uint16)
+    dec = codes.view(np.float16).astype(np.float32)
+    ok = ~np.isnan(dec)
+    assert np.array_equal(oracle.decode("FP16", codes)[ok], dec[ok])
+    assert np.array_equal(oracle.decode("FP16S", codes)[ok], dec[ok] * np.float32(2.0 ** -15))
+    assert np.all(np.isnan(oracle.decode("FP16", codes)[~ok]))
+
+
+def test_fp16s_scale_constant_is_exact_power_of_two():
+    # the decode scale of Sec. 3.4 is written as a decimal FP32 literal
+    assert np.float32("3.0517578E-5") == np.float32(2.0 ** -15)
+    assert np.float32("0.0078125") == np.float32(2.0 ** -7)
+
+
+def _fp16c_prose(x):
+    """FP32 -> FP16C following the prose of Sec. 3.1.4 step by step, on
+    64-bit integers: add the rounding bit 2^11, split exponent and mantissa,
+    re-bias normalised numbers by 127-15 = 112, shift denormalised ones
+    (with the leading one added as 0x800000 - 0x800) right by one place less
+    than needed, add one, shift the last place, saturate above the maximum."""
+    b = (x.view(np.uint32).astype(np.uint64) + 0x800) & 0xFFFFFFFF
+    sign = (b >> 16) & 0x8000
+    e = (b >> 23) & 0xFF
+    m = b & 0x7FFFFF
+    normal = (((e - 112) << 11) & 0x7800) | (m >> 12)
+    shift = 124 - e.astype(np.int64)
+    mm = (0x7FF800 + m)
+    den = np.where((shift >= 0) & (shift < 64),
+                   ((mm >> np.clip(shift, 0, 63).astype(np.uint64)) + 1) >> 1, 0)
+    mag = np.where(e > 112, normal, den)
+    mag = np.where(e > 127, 0x7FFF, mag)
+    return (sign | mag).astype(np.uint16)
+
+
+def test_fp16c_matches_prose_algorithm():
+    rng = np.random.default_rng(11)
+    bits = np.concatenate([
+        np.arange(0, 1 << 32, 4099, dtype=np.uint64).astype(np.uint32),
+        # dense scans across the denormal / normal / saturation boundaries
+        np.arange(0x32000000, 0x32100000, dtype=np.uint32),   # ~2^-27
+        np.arange(0x387F0000, 0x38810000, dtype=np.uint32),   # 2^-14
+        np.arange(0x3FFF0000, 0x40010000, dtype=np.uint32),   # 2
+        rng.integers(0, 1 << 32, 1 << 20, dtype=np.uint64).astype(np.uint32),
+    ])
+    bits = np.concatenate([bits, bits | np.uint32(0x80000000)])
+    x = bits.view(np.float32)
+    x = x[~np.isnan(x)]
+    assert np.array_equal(oracle.encode("FP16C", x), _fp16c_prose(x))
+
+
+# regular rounding range (log2 bounds) where "nearest value, ties away from
+# zero" holds; outside it the documented end rules apply
+REGULAR = {
+    "FP16C": (-26, 1), "P16_0": (-15, 14), "P16_0S": (-22, 7),
+    "P16_1": (-26, 26), "P16_1S": (-33, 19), "P16_2C": (-51, 0.999),
+}
+
+
+@pytest.mark.parametrize("fmt", sorted(REGULAR))
+def test_encode_is_nearest_value_ties_away(fmt):
+    lo, hi = REGULAR[fmt]
+    t = table(fmt)
+    rng = np.random.default_rng(3)
+    x = np.abs(_interesting_floats(rng, lo, hi))
+    u = np.unique(t)
+    mids = ((u[:-1] + u[1:]) / 2)
+    mids = mids[(mids >= 2.0 ** lo) & (mids < 2.0 ** hi)]
+    mids32 = mids.astype(np.float32)
+    mids32 = mids32[mids32.astype(np.float64) == mids]          # exact midpoints only
+    x = np.concatenate([x, mids32, np.nextafter(mids32, 0), np.nextafter(mids32, 2)])
+    if fmt == "P16_2C":
+        x = x[x < 2 - 2.0 ** -13]
+    x = x[(x >= 2.0 ** lo) & (x < 2.0 ** hi)]
+    codes = oracle.encode(fmt, x)
+    got = t[codes & 0x7FFF]
+    xd = x.astype(np.float64)
+    k = np.searchsorted(u, xd, side="right")
+    below = u[np.clip(k - 1, 0, len(u) - 1)]
+    above = u[np.clip(k, 0, len(u) - 1)]
+    expect = np.where(xd - below < above - xd, below, above)   # ties -> above (away from 0)
+    expect = np.where(below == xd, xd, expect)
+    assert np.array_equal(got, expect)
+    neg = oracle.encode(fmt, -x)
+    assert np.array_equal(neg, codes | 0x8000)
+
+
+def test_posit_end_rules():
+    p = lambda e: np.float32(2.0 ** e)
+    enc = lambda f, v: int(oracle.encode(f, np.array([v], dtype=np.float32))[0])
+    # P16_0: half of the smallest value rounds up to it, below rounds to zero
+    assert enc("P16_0", p(-15)) == 1 and enc("P16_0", np.nextafter(p(-15), 0)) == 0
+    assert enc("P16_0", p(14)) == 0x7FFF and enc("P16_0", np.float32(3e38)) == 0x7FFF
+    # P16_1: bit-string rounding where the exponent bit does not fit
+    assert enc("P16_1", p(-30)) == 1 and enc("P16_1", np.nextafter(p(-30), 0)) == 0
+    assert enc("P16_1", np.nextafter(p(-27), 0)) == 1 and enc("P16_1", p(-27)) == 2
+    assert enc("P16_1", np.nextafter(p(27), 0)) == 0x7FFE and enc("P16_1", p(27)) == 0x7FFF
+    # P16_2C: the end rules
+    assert enc("P16_2C", np.nextafter(p(-58), 0)) == 0 and enc("P16_2C", p(-58)) == 2
+    assert enc("P16_2C", p(-55)) == 3 and enc("P16_2C", p(-53)) == 4
+    assert enc("P16_2C", np.float32(2 - 2.0 ** -13)) == 0
+    assert enc("P16_2C", np.float32(2.0)) == 0x7FFF
+    for f in ("P16_0", "P16_1", "P16_2C", "FP16C"):
+        assert enc(f, np.float32(np.inf)) == 0x7FFF and enc(f, np.float32(-np.inf)) == 0xFFFF
+
+
+@pytest.mark.parametrize("row", golden("posit_accuracy_intervals.txt"), ids=lambda r: "-".join(r[:2]))
+def test_sec322_accuracy_intervals(row):
+    """Within [2^lo, 2^hi) the posit's value spacing is no larger than the
+    compared format's in every binade, and larger in the binades just outside."""
+    fmt, other, lo, hi = row[0], row[1], int(row[2]), int(row[3])
+
+    def spacing(f, e):
+        t = np.unique(table(f))
+        t = t[np.isfinite(t)]
+        inb = t[(t >= 2.0 ** e) & (t < 2.0 ** (e + 1))]
+        return np.diff(np.concatenate([inb, t[t >= 2.0 ** (e + 1)][:1]])).max()
+
+    for e in range(lo, hi):
+        assert spacing(fmt, e) <= spacing(other, e), e
+    assert spacing(fmt, lo - 1) > spacing(other, lo - 1)
+    if hi <= 0:
+        assert spacing(fmt, hi) > spacing(other, hi)
+
+
+def test_fp16c_nan_rule():
+    """NaN inputs: the rounding increment wraps the top 2048 NaN patterns of
+    each sign to a zero of the other sign; other NaNs saturate (a reading of
+    the conversion routine; the paper defines no NaN behaviour)."""
+    b = np.array([0x7F800001, 0x7FFFF7FF, 0x7FFFF800, 0x7FFFFFFF,
+                  0xFF800001, 0xFFFFF7FF, 0xFFFFF800, 0xFFFFFFFF], dtype=np.uint32)
+    got = oracle.encode("FP16C", b.view(np.float32)).tolist()
+    assert got == [0x7FFF, 0x7FFF, 0x8000, 0x8000, 0xFFFF, 0xFFFF, 0x0000, 0x0000]

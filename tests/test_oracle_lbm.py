@@ -1,0 +1,261 @@
+"""Pins of the oracle's lattice Boltzmann step against closed forms, invariants
+and values printed in the paper.
+
+A plausible mistake in the oracle (a dropped term, a wrong sign or index, a
+transposed weight, a wrong relaxation factor) changes at least one of:
+equilibrium moments, Table 1's bound, conservation, the Guo momentum input,
+the exact TRT / magic-tau Poiseuille parabola, the Poiseuille start-up series,
+the Taylor-Green decay rate (which fixes nu = (tau - 1/2)/3), Couette flow, or
+the uniform open channel.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from conftest import golden
+
+VELSETS = ["D2Q9", "D3Q19", "D3Q27"]
+
+
+@pytest.mark.parametrize("vs", VELSETS)
+@pytest.mark.parametrize("arith,tol", [("DEF64", 2e-15), ("ORD64", 2e-15), ("ORD32", 2e-6)])
+def test_equilibrium_moments(vs, arith, tol):
+    """Sec. 2.2: sum_i f^eq-s = rho - 1, sum_i c_i f^eq-s = rho u and
+    sum_i c_i c_i f^eq-s = rho u u + (rho - 1) c^2 I (weights moved out by the shift)."""
+    c, w = oracle.velset(vs)
+    d = 2 if vs == "D2Q9" else 3
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        rho = 1 + 0.2 * rng.uniform(-1, 1)
+        u = 0.1 * rng.uniform(-1, 1, 3)
+        if d == 2:
+            u[2] = 0
+        f = oracle.equilibrium(vs, arith, rho, u)
+        assert abs(f.sum() - (rho - 1)) <= tol
+        assert np.allclose(c.T @ f, rho * u, rtol=0, atol=tol)
+        P = (c[:, :, None] * c[:, None, :] * f[:, None, None]).sum(0)
+        expect = rho * np.outer(u, u) + (rho - 1) / 3 * np.eye(3)
+        if d == 2:
+            expect[2, 2] = 0
+        assert np.allclose(P, expect, rtol=0, atol=5 * tol)
+
+
+def test_weights_sum_and_isotropy():
+    for vs in VELSETS:
+        c, w = oracle.velset(vs)
+        assert abs(w.sum() - 1) < 1e-15
+        d = 2 if vs == "D2Q9" else 3
+        M2 = (w[:, None, None] * c[:, :, None] * c[:, None, :]).sum(0)
+        assert np.allclose(M2[:d, :d], np.eye(d) / 3, atol=1e-15)
+        for i in range(1, len(w), 2):        # 2k-1 and 2k are opposite
+            assert np.array_equal(c[i], -c[i + 1])
+
+
+@pytest.mark.parametrize("row", golden("delta_table1.txt"), ids=lambda r: r[0])
+def test_table1_delta_shifted(row):
+    """Table 1: max |f^eq-s| / rho over u_j = c c_j/|c_j| rounds up to the printed value."""
+    vs, printed = row[0], float(row[1])
+    c, w = oracle.velset(vs)
+    best = 0.0
+    for j in range(1, len(w)):
+        u = c[j] / np.linalg.norm(c[j]) / math.sqrt(3)
+        best = max(best, np.abs(oracle.equilibrium(vs, "DEF64", 1.0, u)).max())
+    assert printed - 0.01 < best <= printed
+    assert math.ceil(best * 100 - 1e-9) / 100 == pytest.approx(printed)
+
+
+@pytest.mark.parametrize("vs", VELSETS)
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+@pytest.mark.parametrize("arith", ["DEF64", "ORD64"])
+def test_collision_conserves_mass_and_momentum(vs, coll, arith):
+    c, w = oracle.velset(vs)
+    q = len(w)
+    rng = np.random.default_rng(2)
+    L = oracle.Lattice(1, 1, 1, vs, coll, arith, "FP64", tau=0.63, trt_lambda=0.25)
+    for _ in range(5):
+        f = rng.uniform(-0.02, 0.02, (q, 1, 1, 1))
+        L.set_f(f)
+        L.step(1)
+        g = L.f().reshape(q)
+        assert abs(g.sum() - f.sum()) < 1e-15
+        assert np.allclose(c.T @ g, c.T @ f.reshape(q), rtol=0, atol=1e-16)
+        assert not np.allclose(g, f.reshape(q))     # something did relax
+
+
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+def test_guo_force_adds_F_per_step(coll):
+    F = (1e-5, -2e-5, 3e-5)
+    L = oracle.Lattice(6, 5, 4, "D3Q19", coll, "DEF64", "FP64", tau=0.7, force=F)
+    L.set_rho_u(*W.random_fields((4, 5, 6), 3))
+    L.step(1)
+
+    def momentum():
+        r, ux, uy, uz = L.rho_u()
+        return np.array([(r * ux).sum(), (r * uy).sum(), (r * uz).sum()])
+
+    p0 = momentum()
+    L.step(10)
+    assert np.allclose((momentum() - p0) / (6 * 5 * 4 * 10), F, rtol=1e-10, atol=0)
+
+
+@pytest.mark.parametrize("vs,shape", [("D2Q9", (1, 12, 14)), ("D3Q19", (6, 7, 9)), ("D3Q27", (5, 6, 7))])
+def test_periodic_and_bounce_back_mass_conservation(vs, shape):
+    nz, ny, nx = shape
+    rng = np.random.default_rng(9)
+    flags = np.where(rng.uniform(size=shape) < 0.1, W.WALL, 0).astype(np.uint8)
+    L = oracle.Lattice(nx, ny, nz, vs, "SRT", "DEF64", "FP64", tau=0.6)
+    L.set_geometry(flags)
+    L.set_rho_u(*W.random_fields(shape, 4))
+    m0, _ = L.reduce()
+    L.step(300)
+    m1, _ = L.reduce()
+    assert abs(m1 / m0 - 1) < 1e-13
+
+
+def _startup_series(F, nu, H, eta, t, terms=400):
+    u = F / (2 * nu) * eta * (H - eta)
+    for n in range(1, 2 * terms, 2):
+        u -= 4 * F * H * H / (nu * math.pi ** 3 * n ** 3) * np.sin(n * math.pi * eta / H) * \
+            math.exp(-nu * n * n * math.pi ** 2 * t / (H * H))
+    return u
+
+
+def test_poiseuille_plate_startup_series():
+    """Plane Poiseuille flow from rest, walls half-way at y = 0.5 and ny - 1.5:
+    u(eta, t) = F eta (H - eta)/(2 nu) - sum_odd 4 F H^2/(nu pi^3 n^3) sin(n pi eta/H) e^{-nu n^2 pi^2 t/H^2}.
+    The 64-cell plate of the 8x64x8 workload (x and z periodic, so one column
+    carries the same flow); BGK bounce-back slip keeps the error near 1e-4."""
+    tau, F, ny, T = 0.8, 1e-6, 64, 10000
+    L = oracle.Lattice(1, ny, 1, "D3Q19", "SRT", "DEF64", "FP64", tau=tau, force=(F, 0, 0))
+    L.set_geometry(W.poiseuille_plate(1, ny, 1))
+    L.set_rho_u()
+    L.step(T)
+    _, ux, _, _ = L.rho_u()
+    nu, H = (tau - 0.5) / 3, ny - 2
+    eta = np.arange(1, ny - 1) - 0.5
+    ref = _startup_series(F, nu, H, eta, T)
+    err = np.sqrt(((ux[0, 1:-1, 0] - ref) ** 2).sum() / (ref ** 2).sum())
+    assert err < 3e-4
+
+
+@pytest.mark.parametrize("coll,tau", [("TRT", 0.8), ("SRT", 0.5 + math.sqrt(3) / 4)])
+def test_poiseuille_exact_at_magic_parameter(coll, tau):
+    """With Lambda = (tau+ - 1/2)(tau- - 1/2) = 3/16, half-way bounce-back sits
+    exactly mid-grid and the steady force-driven profile is the exact parabola."""
+    F, ny = 1e-6, 34
+    L = oracle.Lattice(1, ny, 1, "D3Q19", coll, "DEF64", "FP64", tau=tau, trt_lambda=3 / 16, force=(F, 0, 0))
+    L.set_geometry(W.poiseuille_plate(1, ny, 1))
+    L.set_rho_u()
+    L.step(60000)
+    _, ux, _, _ = L.rho_u()
+    nu, H = (tau - 0.5) / 3, ny - 2
+    eta = np.arange(1, ny - 1) - 0.5
+    ref = F / (2 * nu) * eta * (H - eta)
+    assert np.abs(ux[0, 1:-1, 0] - ref).max() / ref.max() < 1e-11
+
+
+def test_couette_linear_profile():
+    """Moving bounce-back (Ladd, rho_w = 1): steady shear flow is linear."""
+    U, ny = 0.01, 18
+    flags, node_u = W.couette_plate(1, ny, 1, U)
+    for tau in (0.6, 1.0, 1.7):
+        L = oracle.Lattice(1, ny, 1, "D3Q19", "SRT", "DEF64", "FP64", tau=tau)
+        L.set_geometry(flags, node_u)
+        L.set_rho_u()
+        L.step(40000)
+        _, ux, _, _ = L.rho_u()
+        eta = np.arange(1, ny - 1) - 0.5
+        assert np.abs(ux[0, 1:-1, 0] - U * eta / (ny - 2)).max() / U < 1e-6
+
+
+@pytest.mark.parametrize("vs,nz", [("D2Q9", 1), ("D3Q19", 2), ("D3Q27", 2)])
+def test_taylor_green_decay_rate(vs, nz):
+    """Sec. 4.2: E(t) = E0 exp(-4 nu k^2 t) with nu = (tau - 1/2)/3."""
+    n, tau, u0, T = 64, 0.8, 0.01, 400
+    L = oracle.Lattice(n, n, nz, vs, "SRT", "DEF64", "FP64", tau=tau)
+    L.set_rho_u(*W.taylor_green_extruded(n, u0, nz=nz))
+    _, E0 = L.reduce()
+    L.step(T)
+    _, E1 = L.reduce()
+    nu, k = (tau - 0.5) / 3, 2 * math.pi / n
+    rate = -math.log(E1 / E0) / T
+    assert abs(rate / (4 * nu * k * k) - 1) < 2e-3
+
+
+def test_open_channel_stays_uniform():
+    """Equilibrium inflow, zero-gradient outflow and free-slip walls leave a
+    uniform stream uniform."""
+    nx, ny, nz = 20, 8, 3
+    u = float(np.float32(0.05))
+    flags, node_u, node_rho = W.karman_channel(nx, ny, nz, radius=0, cx=-100, cy=-100, u_in=u)
+    L = oracle.Lattice(nx, ny, nz, "D3Q19", "SRT", "DEF64", "FP64", tau=0.6)
+    L.set_geometry(flags, node_u, node_rho)
+    L.set_rho_u(np.ones((nz, ny, nx)), np.full((nz, ny, nx), u), None, None)
+    L.step(200)
+    r, ux, uy, uz = L.rho_u()
+    fl = flags == 0
+    assert np.abs(ux[fl] - u).max() < 1e-14
+    assert np.abs(r[fl] - 1).max() < 1e-14
+    assert np.abs(uy[fl]).max() < 1e-14
+
+
+def test_freeslip_is_mirror_and_bounce_back_is_reversal():
+    """One streaming step next to a free-slip wall (normal y) returns the
+    mirrored population of the neighbouring column; next to a plain wall the
+    cell's own opposite population."""
+    nx, ny, nz = 4, 3, 1
+    c, w = oracle.velset("D2Q9")
+    for kind in ("freeslip", "wall"):
+        flags = np.zeros((nz, ny, nx), np.uint8)
+        flags[:, 0, :] = W.freeslip(1) if kind == "freeslip" else W.WALL
+        L = oracle.Lattice(nx, ny, nz, "D2Q9", "SRT", "DEF64", "FP64", tau=1.0)
+        L.set_geometry(flags)
+        rng = np.random.default_rng(1)
+        f = rng.uniform(-0.01, 0.01, (9, nz, ny, nx))
+        f[:, flags != 0] = 0
+        L.set_f(f)
+        g = L.f()
+        x, y = 1, 1
+        for i in range(9):
+            if c[i][1] != 1:          # only populations coming out of the y = 0 wall
+                continue
+            if kind == "freeslip":
+                j = [k for k in range(9) if c[k][0] == c[i][0] and c[k][1] == -c[i][1]][0]
+                assert g[i, 0, y, x] == f[j, 0, y, x - c[i][0]]
+            else:
+                j = [k for k in range(9) if np.array_equal(c[k], -c[i])][0]
+                assert g[i, 0, y, x] == f[j, 0, y, x]
+
+
+@pytest.mark.parametrize("vs", VELSETS)
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+def test_ordered_modes_track_definition(vs, coll):
+    """The paper's operation order changes results only by rounding."""
+    shape = (1, 9, 11) if vs == "D2Q9" else (5, 6, 7)
+    flags, node_u, node_rho = W.random_geometry(shape, 12)
+    out = {}
+    for arith, storage in (("DEF64", "FP64"), ("ORD64", "FP64"), ("ORD32", "FP32")):
+        L = oracle.Lattice(shape[2], shape[1], shape[0], vs, coll, arith, storage, tau=0.7,
+                           force=(1e-5, 2e-5, 0 if vs == "D2Q9" else -1e-5))
+        L.set_geometry(flags, node_u, node_rho)
+        L.set_rho_u(*W.random_fields(shape, 13))
+        L.step(40)
+        out[arith] = L.f()
+    ref = out["DEF64"]
+    scale = np.abs(ref).max()
+    assert np.abs(out["ORD64"] - ref).max() / scale < 1e-13
+    assert np.abs(out["ORD32"] - ref).max() / scale < 2e-5
+
+
+@pytest.mark.parametrize("fmt", oracle.CODEC_FORMATS)
+def test_sixteen_bit_storage_holds_codec_values(fmt):
+    """In ORD32 mode every stored population is a decoded code of the format."""
+    shape = (3, 4, 5)
+    L = oracle.Lattice(5, 4, 3, "D3Q19", "SRT", "ORD32", fmt, tau=0.8)
+    L.set_rho_u(*W.random_fields(shape, 1))
+    L.step(3)
+    f = L.f().astype(np.float32).reshape(-1)
+    assert np.array_equal(oracle.decode(fmt, oracle.encode(fmt, f)), f)
