@@ -1,0 +1,372 @@
+"""Benchmark of the fused D3Q19 stream-collide step on one or more GB300s.
+
+Workload (one bench "step" = one time step of the whole lattice): D3Q19 SRT
+3-D Taylor-Green vortex on a fully periodic 256^3 lattice (u0 = 0.05,
+tau = 0.53), initial fields from the closed form, A-B streaming, flag-free
+periodic kernel -- the paper's benchmark box (Sec. 5: periodic cube, no
+boundary nodes, 256^3).  The headline tier is FP32 arithmetic with FP16S
+storage (`--format`); every other storage tier is measured on the same
+workload in `per_format`, and the batched ensemble of lid-driven cavities
+(512 cubes, edges 16..128, FP16S) against one launch per member in
+`ensemble`.  Inputs are resident in HBM for `value`; `e2e` goes through the
+C ABI with pinned host buffers.  Under torchrun each rank advances its own
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D3Q19 MLUPs/s per storage format vs HBM roofline; ensemble MLUPs/s vs per-launch"
+PAPER_A100_FP16S = 15455.0   # MLUPs/s, Nvidia A100 40GB, FP32/FP16S, D3Q19 SRT 256^3 (Table 5)
+TIERS = [  # (name, arithmetic, storage)
+    ("FP64/FP64", "FP64", "FP64"), ("FP64/FP32", "FP64", "FP32"), ("FP32/FP32", "FP32", "FP32"),
+    ("FP32/FP16", "FP32", "FP16"), ("FP32/FP16S", "FP32", "FP16S"), ("FP32/FP16C", "FP32", "FP16C"),
+    ("FP32/P16_0S", "FP32", "P16_0S"), ("FP32/P16_1S", "FP32", "P16_1S"), ("FP32/P16_2C", "FP32", "P16_2C"),
+    ("FP32/P16_0", "FP32", "P16_0"), ("FP32/P16_1", "FP32", "P16_1"),
+]
+BYTES_PER_POP = {"FP64": 8, "FP32": 4}
+
+
+def pop_bytes(storage):
+    return BYTES_PER_POP.get(storage, 2)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for n in ("lbm_kernels.cuh", "lbm_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2112_08926_gb300", "csrc", n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(tier):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "stream_collide_d3q19_tgv256_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    with open(path) as fh:
+        for line in fh:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == tier and parts[1] == want:
+                return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+        return False
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def tg_fields(n):
+    import workloads as W
+    return W.taylor_green_3d(n, 0.05)
+
+
+def make_lattice(P, n, arith, storage, scheme="AB", fields=None):
+    g = P.Lattice(n, n, n, "D3Q19", "SRT", storage, arith, scheme, tau=0.53)
+    if fields is not None:
+        g.set_rho_u(*fields)
+    return g
+
+
+def time_steps(torch, g, steps):
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    s0.record()
+    g.step(steps)
+    s1.record()
+    torch.cuda.synchronize()
+    return s0.elapsed_time(s1) / 1e3
+
+
+def cpu_baseline(n, storage, budget_s=10.0):
+    """The oracle (FP32 arithmetic in the paper's order + the storage codec),
+    as it stands, on a bounded sample: whole steps of the same lattice until
+    ~budget_s of CPU time."""
+    import oracle
+    import workloads as W
+    o = oracle.Lattice(n, n, n, "D3Q19", "SRT", "ORD32", storage, tau=0.53)
+    o.set_rho_u(*W.taylor_green_3d(n, 0.05))
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    k = max(1, min(50, int(budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * k / dt / 1e6, "unit": "MLUPs/s", "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{k} oracle steps (after 1 warm-up) of the same D3Q19 SRT TGV {n}^3 lattice, "
+                      f"FP32 ordered arithmetic with {storage} storage"}
+
+
+def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
+    import workloads as W
+    specs = W.ensemble_cavities(count=count, seed=seed)
+    cells = sum(s.n ** 3 for s in specs)
+
+    def build():
+        mem = []
+        for s in specs:
+            g = P.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=s.tau)
+            flags, node_u = W.cavity(s.n, s.u_lid)
+            g.set_geometry(flags, node_u)
+            g.set_rho_u()
+            mem.append(g)
+        return mem
+
+    mem = build()
+    e = P.Ensemble(mem)
+    bx, by = e.autotune(trial_steps=3)
+    e.step(warmup)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize()
+    ev[0].record()
+    e.step(steps)
+    ev[1].record()
+    e.step_each(warmup)
+    torch.cuda.synchronize()
+    ev[2].record()
+    e.step_each(steps)
+    ev[3].record()
+    torch.cuda.synchronize()
+    t_b = ev[0].elapsed_time(ev[1]) / 1e3
+    t_e = ev[2].elapsed_time(ev[3]) / 1e3
+    e.close()
+    for g in mem:
+        g.close()
+    return {"workload": f"{count} D3Q19 SRT lid-driven cavities, edges U{{16..128}} (splitmix64 seed {seed}), "
+                        f"tau U[0.51,0.9], lid U[0.02,0.1], FP32/FP16S, A-B",
+            "cells": cells, "steps": steps, "tile": [bx, by],
+            "batched_mlups": cells * steps / t_b / 1e6, "per_launch_mlups": cells * steps / t_e / 1e6,
+            "speedup": t_e / t_b, "launches_per_step": {"batched": 1, "per_launch": count}}
+
+
+def bench_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    import workloads as W
+    n = 64
+    o = oracle.Lattice(n, n, n, "D3Q19", "SRT", "ORD32", args.format, tau=0.53)
+    o.set_rho_u(*W.taylor_green_3d(n, 0.05))
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = n ** 3 * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "MLUPs/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"D3Q19 SRT Taylor-Green vortex, periodic, {args.size}^3 (sample {n}^3)",
+                   "storage": args.format, "arithmetic": "FP32", "scheme": "AB"},
+        "cpu_baseline": {"value": v, "unit": "MLUPs/s", "kind": "oracle", "cores": oracle.threads(),
+                         "sample": f"each step one oracle step of a {n}^3 periodic D3Q19 SRT TGV lattice "
+                                   f"(FP32 ordered arithmetic, {args.format} storage)"},
+        "e2e": {"value": v, "unit": "MLUPs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=int(os.environ.get("WORLD_SIZE", "1")))
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--format", default="FP16S")
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--scheme", default="AB", choices=["AB", "AA"])
+    ap.add_argument("--no-sweep", action="store_true", help="headline tier only")
+    ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        bench_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2112_08926_gb300 as P
+
+    n = args.size
+    N = n ** 3
+    fields = tg_fields(n)
+    head_arith = "FP64" if args.format == "FP64" else "FP32"
+    g = make_lattice(P, n, head_arith, args.format, args.scheme, fields)
+    g.step(args.warmup)
+    m0, _ = g.reduce()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        gpu_id = str(local)
+    with ClockSampler(gpu_id) as clk:
+        elapsed = time_steps(torch, g, args.steps)
+    if dist:
+        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    m1, e1 = g.reduce()
+    value = world * N * args.steps / elapsed / 1e6
+    ms = elapsed / args.steps * 1e3
+    bpc = 2 * 19 * pop_bytes(args.format)
+    peak, peak_kind = peaks()
+    achieved = bpc * N / (elapsed / args.steps) / 1e9
+    tier_name = f"{head_arith}/{args.format}"
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": profiled_traffic(tier_name), "peak_kind": peak_kind,
+                "bytes_per_cell": bpc, "kernel": "k_step<D3Q19,SRT,%s,A-B,flag-free>" % args.format}
+
+    # end to end through the C ABI with pinned host buffers
+    pin = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).pin_memory() for a in fields]
+    outs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(4)]
+    g.set_rho_u_ptr(*[p.data_ptr() for p in pin])
+    g.step(args.warmup)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g.set_rho_u_ptr(*[p.data_ptr() for p in pin])
+    g.step(args.steps)
+    g.get_rho_u_ptr(*[o.data_ptr() for o in outs])
+    torch.cuda.synchronize()
+    e2e_t = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    g.close()
+    e2e = {"value": world * N * args.steps / e2e_t / 1e6, "unit": "MLUPs/s",
+           "h2d_bytes_per_step": 4 * N * 8 / args.steps, "d2h_bytes_per_step": 4 * N * 8 / args.steps}
+
+    per_format, ens, cpu = None, None, None
+    if rank == 0 and world == 1:
+        if not args.no_sweep:
+            per_format = {}
+            for name, arith, storage in TIERS:
+                steps = max(args.steps // (8 if arith == "FP64" else 2), 10)
+                gg = make_lattice(P, n, arith, storage, "AB", fields)
+                gg.step(args.warmup)
+                dt = time_steps(torch, gg, steps)
+                b = 2 * 19 * pop_bytes(storage)
+                per_format[name] = {"mlups": N * steps / dt / 1e6, "gbs": b * N * steps / dt / 1e9,
+                                    "frac_hbm": b * N * steps / dt / 1e9 / peak, "bytes_per_cell": b,
+                                    "roofline_mlups": peak * 1e3 / b, "steps": steps}
+                gg.close()
+            gg = make_lattice(P, n, head_arith, args.format, "AA", fields)
+            gg.step(args.warmup)
+            steps = max(args.steps // 2, 10)
+            dt = time_steps(torch, gg, steps)
+            per_format[f"{tier_name} A-A"] = {"mlups": N * steps / dt / 1e6,
+                                              "frac_hbm": bpc * N * steps / dt / 1e9 / peak,
+                                              "bytes_per_cell": bpc, "steps": steps}
+            gg.close()
+        if not args.no_ensemble:
+            ens = run_ensemble(P, torch, steps=max(20, min(args.steps // 20, 100)), warmup=args.warmup)
+        if not args.no_cpu:
+            cpu = cpu_baseline(n, args.format)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "MLUPs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": value / PAPER_A100_FP16S if args.format == "FP16S" else None,
+        "baseline_ref": "paper Table 5, Nvidia A100 40GB, FP32/FP16S, D3Q19 SRT 256^3: 15455 MLUPs/s",
+        "dtype": "f32" if head_arith == "FP32" else "f64", "data": "synthetic",
+        "config": {"workload": f"D3Q19 SRT 3-D Taylor-Green vortex, periodic {n}^3, u0=0.05, tau=0.53",
+                   "storage": args.format, "arithmetic": head_arith, "scheme": args.scheme,
+                   "kernel": "flag-free periodic", "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roofline, "clocks": clk.summary(), "e2e": e2e, "gpu_launches": args.steps,
+        "check": {"mass_rel_drift": abs(m1 / m0 - 1), "kinetic_energy": e1},
+        "cpu_baseline": cpu, "per_format": per_format, "ensemble": ens,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,210 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) mixed-precision lattice Boltzmann library.
+ *
+ * The library implements the fused stream-collide step of Lehmann et al.,
+ * "On the accuracy and performance of the lattice Boltzmann method with
+ * 64-bit, 32-bit and novel 16-bit number formats" (arXiv 2112.08926):
+ * populations (DDFs) are stored shifted (Sec. 2.2) in FP64, FP32 or one of
+ * the 16-bit formats of Sec. 3, while the collision runs in FP32 (or FP64)
+ * registers.  Every step of the path runs in CUDA kernels; the host code only
+ * validates arguments, moves data and launches.
+ *
+ * Conventions shared by every entry point
+ *   - Cell index n = x + nx*(y + ny*z), x fastest (the paper's appendix core
+ *     uses the same linearisation).
+ *   - Host arrays belong to the caller and are read or written before the
+ *     call returns.  Device memory is owned by the handle and obtained
+ *     through the lbm_allocator given at creation (cudaMalloc if NULL).
+ *   - Every call returns an lbm_status; nothing aborts or traps.  After a
+ *     CUDA error the handle is poisoned: later calls return LBM_ERR_STATE and
+ *     lbm_last_error() describes the first failure.
+ *   - Velocity-set directions: 0 is rest, 2k-1 and 2k are opposite; D3Q19 in
+ *     the order of the paper's D3Q19 core (+x -x +y -y +z -z, ++0 --0, +0+
+ *     -0-, 0++ 0--, +-0 -+0, +0- -0+, 0+- 0-+); D3Q27 appends +++ ---, ++-
+ *     --+, +-+ -+-, -++ +--; D2Q9 is 0, +x -x +y -y, ++ --, +- -+.
+ *   - Populations are stored population-major (structure of arrays,
+ *     f[i*N + n]); q*N codes per copy.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = 1,          /* invalid argument (reason in lbm_last_error) */
+    LBM_ERR_OOM = 2,          /* the allocator returned NULL */
+    LBM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
+    LBM_ERR_UNSUPPORTED = 4,  /* valid but unsupported combination */
+    LBM_ERR_DIVERGED = 5,     /* FP64 mass check found a non-finite value */
+    LBM_ERR_TIMEOUT = 6,      /* reserved */
+    LBM_ERR_STATE = 7         /* handle poisoned by an earlier CUDA error */
+} lbm_status;
+
+/* velocity sets (Sec. 2.1; D3Q19 main, D2Q9 and D3Q27 variants) */
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
+/* collision operators (Sec. 2.1: single- and two-relaxation-time) */
+enum { LBM_SRT = 0, LBM_TRT = 1 };
+/* storage formats of the populations (Sec. 3, Table 2).  P16_0 / P16_1 are
+ * the posit formats of Sec. 3.2 without the 2^7 scaling. */
+enum {
+    LBM_FP64 = 0, LBM_FP32 = 1, LBM_FP16 = 2, LBM_FP16S = 3, LBM_FP16C = 4,
+    LBM_P16_0S = 5, LBM_P16_1S = 6, LBM_P16_2C = 7, LBM_P16_0 = 8, LBM_P16_1 = 9
+};
+/* arithmetic precision of the collision (the "FPa" of the paper's "FPa/FPs") */
+enum { LBM_ARITH_FP32 = 0, LBM_ARITH_FP64 = 1 };
+/* streaming scheme: one-step pull with two copies (A-B, Sec. 5) or the
+ * in-place A-A scheme with one copy (Sec. 1 "any swap algorithm") */
+enum { LBM_STREAM_AB = 0, LBM_STREAM_AA = 1 };
+
+/* cell flag bits (one byte per cell) */
+#define LBM_FLUID        0x00u
+#define LBM_WALL         0x01u  /* solid: mid-grid bounce-back (Sec. 4.1) */
+#define LBM_MOVING       0x02u  /* with WALL: moving bounce-back (Sec. 4.4), velocity in node_u */
+#define LBM_EQ           0x04u  /* equilibrium boundary node (Sec. 4.3): node_rho, node_u */
+#define LBM_OUTFLOW      0x08u  /* zero-gradient outflow: copies the -x neighbour's inflow */
+#define LBM_FREESLIP     0x10u  /* with WALL: specular wall, normal axis in bits 5-6 */
+#define LBM_FREESLIP_AXIS(a) ((uint8_t)(LBM_WALL | LBM_FREESLIP | ((a) << 5)))
+
+typedef struct {
+    int nx, ny, nz;     /* lattice size; D2Q9 requires nz == 1 */
+    int velset;         /* LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 */
+    int collision;      /* LBM_SRT, LBM_TRT */
+    int storage;        /* LBM_FP64 .. LBM_P16_1 */
+    int arith;          /* LBM_ARITH_FP32; LBM_ARITH_FP64 only with FP64/FP32 storage */
+    int scheme;         /* LBM_STREAM_AB, LBM_STREAM_AA */
+    double tau;         /* relaxation time (> 0.5); omega = 1/tau (appendix, SRT) */
+    double trt_lambda;  /* TRT magic parameter (tau+ - 1/2)(tau- - 1/2), e.g. 3/16 */
+    double force[3];    /* Guo body force per volume (Sec. 4.1); D2Q9 ignores z */
+} lbm_params;
+
+typedef struct {
+    /* Returns device memory of `bytes` bytes (256-byte aligned) or NULL. */
+    void* (*alloc)(size_t bytes, void* ctx);
+    void (*release)(void* ptr, void* ctx);
+    void* ctx;
+} lbm_allocator;
+
+typedef struct lbm_handle lbm_handle;
+
+/* Create a lattice.  Allocates the population copies (one for A-A, two for
+ * A-B), flags and boundary-node arrays, and scratch.  All cells start as
+ * fluid with zero populations (rho = 1, u = 0).  cuda_stream is a
+ * cudaStream_t; NULL selects the legacy default stream.
+ * Errors: LBM_ERR_ARG (bad sizes/enums/tau), LBM_ERR_UNSUPPORTED (FP64
+ * arithmetic with 16-bit storage, more than 2^31 cells), LBM_ERR_OOM,
+ * LBM_ERR_CUDA. */
+lbm_status lbm_create(const lbm_params* params, const lbm_allocator* allocator,
+                      void* cuda_stream, lbm_handle** out);
+
+/* Release every device allocation; NULL is accepted. */
+lbm_status lbm_destroy(lbm_handle* h);
+
+/* Cell types and boundary data, host arrays of N = nx*ny*nz cells.
+ * flags: N bytes (NULL: every cell fluid, fully periodic -- the flag-free
+ * kernel of the paper's periodic benchmark box, Sec. 5); node_u: 3*N floats
+ * component-major (ux[N], uy[N], uz[N]; wall velocity of MOVING cells, state
+ * of EQ cells) or NULL (zero); node_rho: N floats (EQ density) or NULL (1).
+ * With A-A streaming, OUTFLOW and FREESLIP cells give LBM_ERR_UNSUPPORTED.
+ * Invalid bit combinations give LBM_ERR_ARG. */
+lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* node_u,
+                            const float* node_rho);
+
+/* Initialise every non-solid cell with the shifted equilibrium (Sec. 2.2)
+ * of the given density and velocity (host arrays of N doubles; NULL means
+ * rho = 1 / u = 0), converted to the arithmetic precision first; solid cells
+ * get zero populations.  Resets the step counter to 0. */
+lbm_status lbm_set_rho_u(lbm_handle* h, const double* rho, const double* ux,
+                         const double* uy, const double* uz);
+
+/* Advance nsteps time steps (each: pull streaming + collision, appendix
+ * "LBM equations in a nutshell", fused in one kernel).  Asynchronous on the
+ * handle's stream. */
+lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
+
+/* Density and velocity of every cell from the streamed populations: rho =
+ * (sum f_i) + 1 (Sec. 2.2), u = (sum c_i f_i + F/2)/rho (not clamped).
+ * EQ cells report their node state, solid cells rho = 1, u = 0.  Host arrays
+ * of N doubles (any may be NULL).  Synchronises the stream. */
+lbm_status lbm_get_rho_u(lbm_handle* h, double* rho, double* ux, double* uy, double* uz);
+
+/* Streamed populations f_i(x) (shifted, decoded, exactly as the next
+ * collision reads them) into a host array of q*N doubles; solid cells 0. */
+lbm_status lbm_get_f(lbm_handle* h, double* f);
+
+/* Overwrite the post-collision populations (what every cell streams out at
+ * the next step) from a host array of q*N doubles, encoded to the storage
+ * format.  Resets the step counter to 0. */
+lbm_status lbm_set_f(lbm_handle* h, const double* f);
+
+/* FP64 sums over non-solid cells of rho and rho |u|^2 / 2 (u with the Guo
+ * half-force), computed on the device.  Returns LBM_ERR_DIVERGED if either
+ * sum is not finite.  Synchronises the stream. */
+lbm_status lbm_reduce(lbm_handle* h, double* mass, double* kinetic_energy);
+
+typedef struct {
+    int q;                    /* populations per cell */
+    int64_t cells;            /* N */
+    int64_t step;             /* steps taken since the last initialisation */
+    int bytes_per_population; /* 8, 4 or 2 */
+    int has_flags;            /* 0: flag-free periodic kernel */
+    size_t device_bytes;      /* bytes held on the device */
+    void* ddf[2];             /* device population copies (ddf[1] NULL for A-A) */
+} lbm_info;
+
+lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info);
+
+/* Thread-block shape of the stream-collide launches (threads along x and y;
+ * bx*by a multiple of 32, at most 1024).  Default 128 x 2. */
+lbm_status lbm_set_block(lbm_handle* h, int bx, int by);
+
+/* Same search as lbm_ensemble_autotune for one lattice; the trial steps
+ * advance the lattice. */
+lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx, int* by);
+
+const char* lbm_last_error(const lbm_handle* h);
+const char* lbm_status_string(lbm_status s);
+
+/* ---- storage codecs as device-array kernels (Sec. 3, Listing 1 formats) -- */
+/* x_dev: n floats, out_dev: n 16-bit codes; storage must be a 16-bit format.
+ * Device pointers, asynchronous on cuda_stream. */
+lbm_status lbm_codec_encode(int storage, const float* x_dev, uint16_t* out_dev, int64_t n,
+                            void* cuda_stream);
+lbm_status lbm_codec_decode(int storage, const uint16_t* c_dev, float* out_dev, int64_t n,
+                            void* cuda_stream);
+/* Encode the floats whose bit patterns are first, first+1, ..., first+n-1. */
+lbm_status lbm_codec_encode_bits(int storage, uint32_t first, int64_t n, uint16_t* out_dev,
+                                 void* cuda_stream);
+
+/* ---- ensembles: many independent lattices advanced by one launch per step -- */
+typedef struct lbm_ensemble lbm_ensemble;
+
+/* Group `count` handles that share velset, collision, storage, arith and
+ * scheme (LBM_ERR_ARG otherwise) and have flags set.  The members keep their
+ * own data; the ensemble adds a device descriptor table and a tile list.
+ * All launches go to the first member's stream. */
+lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out);
+/* Advance every member nsteps steps: one launch per step over all members,
+ * replayed from a CUDA graph of up to 64 steps. */
+lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps);
+/* Same result, one launch per member per step (the baseline). */
+lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps);
+/* Tile shape of the ensemble launch (bx*by a multiple of 32, at most 256). */
+lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by);
+/* Times trial_steps steps for each of a fixed list of tile shapes and keeps
+ * the fastest.  The trial steps are real steps: every member advances by
+ * (trial_steps + 2) * (number of shapes) steps.  Results do not depend on
+ * the tile shape. */
+lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx, int* by);
+lbm_status lbm_ensemble_destroy(lbm_ensemble* e);
+const char* lbm_ensemble_last_error(const lbm_ensemble* e);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_H */

@@ -528,8 +528,11 @@ void orc_set_rho_u(orc_lattice* L, const double* rho, const double* ux, const do
 }
 
 void orc_set_f(orc_lattice* L, const double* f) {
-    const int64_t total = L->vs.q * L->N;
-    for (int64_t k = 0; k < total; ++k) L->fa[k] = quantize(L, f[k]);
+    const int64_t N = L->N;
+    std::fill(L->fb.begin(), L->fb.end(), 0.0);
+    for (int i = 0; i < L->vs.q; ++i)
+        for (int64_t n = 0; n < N; ++n)
+            L->fa[i * N + n] = L->solid(n) ? 0.0 : quantize(L, f[i * N + n]);
 }
 
 void orc_step(orc_lattice* L, int64_t nsteps) {

@@ -91,7 +91,8 @@ void orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u,
 /* initialise every non-solid cell with the shifted equilibrium of (rho, u) */
 void orc_set_rho_u(orc_lattice* L, const double* rho, const double* ux,
                    const double* uy, const double* uz);
-/* overwrite the stored populations (q*N, shifted), quantised to the storage format */
+/* overwrite the stored populations (q*N, shifted), quantised to the storage
+ * format; solid cells are set to zero (their memory is always zero) */
 void orc_set_f(orc_lattice* L, const double* f);
 void orc_step(orc_lattice* L, int64_t nsteps);
 /* density and velocity (incl. the Guo half-force) from the streamed populations */

@@ -1,0 +1,454 @@
+// Device building blocks of the stream-collide step (arXiv 2112.08926):
+// velocity sets, storage codecs of Sec. 3, and the collision of Sec. 2.2 in
+// the operation order the paper prescribes.  Compiled with --fmad=false, so
+// every fused multiply-add below is an explicit fma() and nothing else fuses.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+namespace lbm {
+
+// Compile-time loop: calls f(std::integral_constant<int, I>) for I = B..E-1,
+// so direction indices, velocities and weights are constant expressions.
+template <int B, int E, class F>
+__host__ __device__ __forceinline__ void static_for(F&& f) {
+    if constexpr (B < E) {
+        f(std::integral_constant<int, B>{});
+        static_for<B + 1, E>(f);
+    }
+}
+
+enum : uint32_t {
+    F_WALL = 0x01u, F_MOVING = 0x02u, F_EQ = 0x04u, F_OUTFLOW = 0x08u, F_FREESLIP = 0x10u
+};
+
+// ---------------------------------------------------------------- velocity sets
+// Direction convention: 0 rest, (2k-1, 2k) opposite pairs.  D3Q19 follows the
+// paper's D3Q19 core; D3Q27 appends the corners.
+struct D2Q9 {
+    static constexpr int Q = 9, D = 2, ID = 0;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int t[9][3] = {{0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0},
+                                 {1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 4.0 / 9.0 : (i < 5 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+};
+
+struct D3Q27 {
+    static constexpr int Q = 27, D = 3, ID = 2;
+    __host__ __device__ static constexpr int c(int i, int a) {
+        constexpr int t[27][3] = {
+            {0, 0, 0},
+            {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1},
+            {1, 1, 0}, {-1, -1, 0}, {1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, -1, -1},
+            {1, -1, 0}, {-1, 1, 0}, {1, 0, -1}, {-1, 0, 1}, {0, 1, -1}, {0, -1, 1},
+            {1, 1, 1}, {-1, -1, -1}, {1, 1, -1}, {-1, -1, 1},
+            {1, -1, 1}, {-1, 1, -1}, {-1, 1, 1}, {1, -1, -1}};
+        return t[i][a];
+    }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 8.0 / 27.0 : (i < 7 ? 2.0 / 27.0 : (i < 19 ? 1.0 / 54.0 : 1.0 / 216.0));
+    }
+};
+
+struct D3Q19 {
+    static constexpr int Q = 19, D = 3, ID = 1;
+    __host__ __device__ static constexpr int c(int i, int a) { return D3Q27::c(i, a); }
+    __host__ __device__ static constexpr double w(int i) {
+        return i == 0 ? 1.0 / 3.0 : (i < 7 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+};
+
+__host__ __device__ constexpr int opposite(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
+
+// direction whose velocity is c_i with component `axis` reversed
+template <class V>
+__host__ __device__ constexpr int mirror(int i, int axis) {
+    int r = i;
+    for (int j = 0; j < V::Q; ++j) {
+        bool same = true;
+        for (int a = 0; a < 3; ++a) {
+            const int want = (a == axis) ? -V::c(i, a) : V::c(i, a);
+            if (V::c(j, a) != want) same = false;
+        }
+        if (same) r = j;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- storage codecs
+// Every storage type provides load (code -> arithmetic value) and store
+// (arithmetic value -> code).  The 16-bit codecs are bit-level designs for
+// sm_103a written from the format definitions of Sec. 3; they produce the same
+// codes as the paper's conversion routines but with fewer instructions.
+
+__device__ __forceinline__ uint32_t u32(float x) { return __float_as_uint(x); }
+
+// FP16C (1|4|11, bias 15, Sec. 3.1.2): place the 15 magnitude bits under an
+// FP32 exponent field and multiply by 2^112; exponent 0 lands in the FP32
+// subnormal range and scales to the FP16C subnormals exactly (needs no FTZ).
+__device__ __forceinline__ float fp16c_decode(uint32_t c) {
+    const uint32_t b = ((c & 0x8000u) << 16) | ((c & 0x7FFFu) << 12);
+    return __uint_as_float(b) * 0x1p112f;
+}
+
+// FP32 -> FP16C: round to nearest, halfway cases away from zero, subnormals
+// kept, saturation at the largest magnitude.  Normal range: add half a unit
+// of bit 12 and drop 12 mantissa bits, re-bias the exponent by 127-15.
+// Subnormal range (|x| < 2^-14): the 24-bit significand shifted to units of
+// 2^-25 with a final round-half-up shift.  NaN patterns whose rounding
+// increment would carry into the sign give a zero of the opposite sign.
+__device__ __forceinline__ uint32_t fp16c_encode(float x) {
+    const uint32_t b = u32(x);
+    const uint32_t s = (b >> 16) & 0x8000u;
+    const uint32_t a = b & 0x7FFFFFFFu;
+    const uint32_t norm = min(((a + 0x800u) >> 12) - (112u << 11), 0x7FFFu);
+    const uint32_t E = a >> 23;
+    const uint32_t M = (a & 0x7FFFFFu) | 0x800000u;
+    const uint32_t sh = min(124u - min(E, 124u), 31u);
+    const uint32_t den = ((M >> sh) + 1u) >> 1;
+    uint32_t r = s | (a < 0x38800000u ? den : norm);
+    if (a >= 0x7FFFF800u) r = s ^ 0x8000u;
+    return r;
+}
+
+// length of the regime run of a 15-bit posit magnitude (bits 14..0):
+// leading bits equal to bit 14, at most 15
+__device__ __forceinline__ int posit_run(uint32_t mag) {
+    const uint32_t lead = mag >> 14;
+    const uint32_t t = (mag ^ (0u - lead)) & 0x7FFFu;   // run becomes leading zeros
+    return min(__clz(t << 17), 15);
+}
+
+// Sign-magnitude posit with ES exponent bits (Sec. 3.2.1): regime k = run-1
+// for a run of ones, -run for zeros; value 2^(k*2^ES + e) (1 + fraction).
+// `bias_shift` folds the 2^-7 decode scale of the S variants into the
+// exponent (exact).  Zero magnitude decodes to +-0.
+template <int ES>
+__device__ __forceinline__ float posit_decode(uint32_t c, int bias_shift) {
+    const uint32_t mag = c & 0x7FFFu;
+    const int run = posit_run(mag);
+    const int k = (mag >> 14) ? run - 1 : -run;
+    int e = 0;
+    uint32_t frac;
+    if (ES == 0) {
+        frac = (mag << (run + 9)) & 0x7FFFFFu;
+    } else {
+        e = (int)(((mag << (run + 9)) >> 22) & 1u);
+        frac = (mag << (run + 10)) & 0x7FFFFFu;
+    }
+    const int ex = k * (1 << ES) + e + 127 + bias_shift;
+    const uint32_t bits = ((c & 0x8000u) << 16) | (mag ? (((uint32_t)ex << 23) | frac) : 0u);
+    return __uint_as_float(bits);
+}
+
+// Asymmetric posit P16_2C (Sec. 3.2.2): v leading zeros, a terminating one,
+// two exponent bits, 12-v fraction bits; value 2^(-4v + e - 3)(1 + fraction).
+// With fewer than two exponent bits left (v >= 13) the exponent reads 0.
+__device__ __forceinline__ float p162c_decode(uint32_t c) {
+    const uint32_t mag = c & 0x7FFFu;
+    const int v = min(__clz(mag << 17), 15);
+    const int e = v <= 12 ? (int)((mag >> (12 - v)) & 3u) : 0;
+    const uint32_t frac = (mag << (v + 11)) & 0x7FFFFFu;
+    const uint32_t bits =
+        ((c & 0x8000u) << 16) | (mag ? ((uint32_t)(124 - 4 * v + e) << 23) | frac : 0u);
+    return __uint_as_float(bits);
+}
+
+// mantissa rounded to nf fraction bits (nearest, ties up), added to the
+// regime/exponent pattern R; a carry walks into the next posit value
+__device__ __forceinline__ uint32_t posit_round(uint32_t R, uint32_t m, int nf) {
+    return R + (m >> (23 - nf)) + ((m >> (22 - nf)) & 1u);
+}
+
+// FP32 -> P16_0 (es = 0): nearest value, ties away from zero; 0 below 2^-15,
+// 2^-14 in [2^-15, 2^-14); saturation (also for NaN) from 2^14.
+__device__ __forceinline__ uint32_t p160_encode(float y) {
+    const uint32_t b = u32(y);
+    const uint32_t s = (b >> 16) & 0x8000u;
+    const int E = (int)((b >> 23) & 0xFFu) - 127;
+    const uint32_t m = b & 0x7FFFFFu;
+    uint32_t mag;
+    if (E >= 14) mag = 0x7FFFu;
+    else if (E < -15) mag = 0u;
+    else if (E == -15) mag = 1u;
+    else {
+        const int nf = E >= 0 ? 13 - E : 14 + E;
+        const uint32_t R = E >= 0 ? 0x8000u - (1u << (14 - E)) : 1u << (14 + E);
+        mag = posit_round(R, m, nf);
+    }
+    return s | mag;
+}
+
+// FP32 -> P16_1 (es = 1): nearest value, ties away from zero between 2^-26
+// and 2^26; bit-string rounding where the exponent bit does not fit.
+__device__ __forceinline__ uint32_t p161_encode(float y) {
+    const uint32_t b = u32(y);
+    const uint32_t s = (b >> 16) & 0x8000u;
+    const int E = (int)((b >> 23) & 0xFFu) - 127;
+    const uint32_t m = b & 0x7FFFFFu;
+    uint32_t mag;
+    if (E >= 27) mag = 0x7FFFu;
+    else if (E == 26) mag = 0x7FFEu;
+    else if (E < -30) mag = 0u;
+    else if (E <= -28) mag = 1u;
+    else if (E == -27) mag = 2u;
+    else {
+        const int k = E >> 1;                 // floor(E / 2)
+        const uint32_t ex = (uint32_t)E & 1u;
+        const int nf = k >= 0 ? 12 - k : 13 + k;
+        const uint32_t R = (k >= 0 ? 0x8000u - (1u << (14 - k)) : 1u << (14 + k)) | (ex << nf);
+        mag = posit_round(R, m, nf);
+    }
+    return s | mag;
+}
+
+// FP32 -> P16_2C: nearest value, ties away from zero between 2^-51 and 2;
+// end rules: [2^-53,2^-51) -> 4, [2^-55,2^-53) -> 3, [2^-58,2^-55) -> 2,
+// below -> 0; >= 2 (and NaN) saturate; a rounding carry out of the top
+// binade leaves the 15-bit field (zero).
+__device__ __forceinline__ uint32_t p162c_encode(float x) {
+    const uint32_t b = u32(x);
+    const uint32_t s = (b >> 16) & 0x8000u;
+    const int E = (int)((b >> 23) & 0xFFu) - 127;
+    const uint32_t m = b & 0x7FFFFFu;
+    uint32_t mag;
+    if (E >= 1) mag = 0x7FFFu;
+    else if (E < -58) mag = 0u;
+    else if (E <= -56) mag = 2u;
+    else if (E <= -54) mag = 3u;
+    else if (E <= -52) mag = 4u;
+    else {
+        const int v = (-E) >> 2;
+        const uint32_t ex = 3u - ((uint32_t)(-E) & 3u);
+        const int nf = 12 - v;
+        mag = posit_round((1u << (14 - v)) | (ex << nf), m, nf) & 0x7FFFu;
+    }
+    return s | mag;
+}
+
+template <int FMT> struct Codec16;
+template <> struct Codec16<2> {   // FP16: IEEE binary16, round to nearest even (hardware)
+    __device__ static float dec(uint32_t c) { return __half2float(__ushort_as_half((unsigned short)c)); }
+    __device__ static uint32_t enc(float x) { return __half_as_ushort(__float2half_rn(x)); }
+};
+template <> struct Codec16<3> {   // FP16S: binary16 of x * 2^15 (Sec. 3.1.3)
+    __device__ static float dec(uint32_t c) {
+        return __half2float(__ushort_as_half((unsigned short)c)) * 3.0517578125e-5f;
+    }
+    __device__ static uint32_t enc(float x) { return __half_as_ushort(__float2half_rn(x * 32768.0f)); }
+};
+template <> struct Codec16<4> {   // FP16C (Sec. 3.1.4)
+    __device__ static float dec(uint32_t c) { return fp16c_decode(c); }
+    __device__ static uint32_t enc(float x) { return fp16c_encode(x); }
+};
+template <> struct Codec16<5> {   // P16_0S: posit es=0 of x * 2^7
+    __device__ static float dec(uint32_t c) { return posit_decode<0>(c, -7); }
+    __device__ static uint32_t enc(float x) { return p160_encode(x * 128.0f); }
+};
+template <> struct Codec16<6> {   // P16_1S: posit es=1 of x * 2^7
+    __device__ static float dec(uint32_t c) { return posit_decode<1>(c, -7); }
+    __device__ static uint32_t enc(float x) { return p161_encode(x * 128.0f); }
+};
+template <> struct Codec16<7> {   // P16_2C
+    __device__ static float dec(uint32_t c) { return p162c_decode(c); }
+    __device__ static uint32_t enc(float x) { return p162c_encode(x); }
+};
+template <> struct Codec16<8> {   // P16_0, unscaled
+    __device__ static float dec(uint32_t c) { return posit_decode<0>(c, 0); }
+    __device__ static uint32_t enc(float x) { return p160_encode(x); }
+};
+template <> struct Codec16<9> {   // P16_1, unscaled
+    __device__ static float dec(uint32_t c) { return posit_decode<1>(c, 0); }
+    __device__ static uint32_t enc(float x) { return p161_encode(x); }
+};
+
+// Storage traits: FMT is the lbm.h storage id.
+template <int FMT> struct Storage {
+    using T = uint16_t;
+    static constexpr int bytes = 2;
+    template <class R> __device__ static R load(const T* p, size_t i) { return (R)Codec16<FMT>::dec(p[i]); }
+    template <class R> __device__ static void store(T* p, size_t i, R v) {
+        p[i] = (uint16_t)Codec16<FMT>::enc((float)v);
+    }
+};
+template <> struct Storage<0> {   // FP64
+    using T = double;
+    static constexpr int bytes = 8;
+    template <class R> __device__ static R load(const T* p, size_t i) { return (R)p[i]; }
+    template <class R> __device__ static void store(T* p, size_t i, R v) { p[i] = (double)v; }
+};
+template <> struct Storage<1> {   // FP32
+    using T = float;
+    static constexpr int bytes = 4;
+    template <class R> __device__ static R load(const T* p, size_t i) { return (R)p[i]; }
+    template <class R> __device__ static void store(T* p, size_t i, R v) { p[i] = (float)v; }
+};
+
+// ---------------------------------------------------------------- collision
+__device__ __forceinline__ float fmaR(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmaR(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float minR(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double minR(double a, double b) { return fmin(a, b); }
+__device__ __forceinline__ float maxR(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double maxR(double a, double b) { return fmax(a, b); }
+
+// Relaxation constants in arithmetic precision (computed on the host).
+template <class R> struct Relax {
+    R om, c1, omp, omm, cSp, cSm, cs;
+    R F[3];
+    int force;
+};
+
+// sum over axes of c_ia * v_a in axis order: the first non-zero term is +-v_a,
+// each later one is added or subtracted (no multiplications)
+template <class V, int I, class R>
+__device__ __forceinline__ R csum(const R* v) {
+    constexpr int c0 = V::c(I, 0), c1 = V::c(I, 1), c2 = V::c(I, 2);
+    R s = R(0);
+    if constexpr (c0 != 0) s = c0 > 0 ? v[0] : -v[0];
+    if constexpr (c1 != 0) {
+        if constexpr (c0 == 0) s = c1 > 0 ? v[1] : -v[1];
+        else s = c1 > 0 ? s + v[1] : s - v[1];
+    }
+    if constexpr (c2 != 0) {
+        if constexpr (c0 == 0 && c1 == 0) s = c2 > 0 ? v[2] : -v[2];
+        else s = c2 > 0 ? s + v[2] : s - v[2];
+    }
+    return s;
+}
+
+// alternating-sign momentum sum along axis A over the pairs p..Q-1 (p odd),
+// continuing the running sum s (first: no term yet)
+template <class V, int A, int P, bool FIRST, class R>
+__device__ __forceinline__ R jsum(const R* f, R s) {
+    if constexpr (P >= V::Q) {
+        return s;
+    } else {
+        constexpr int ca = V::c(P, A);
+        if constexpr (ca == 0) {
+            return jsum<V, A, P + 2, FIRST, R>(f, s);
+        } else {
+            constexpr int pos = ca > 0 ? P : P + 1;
+            constexpr int neg = ca > 0 ? P + 1 : P;
+            if constexpr (FIRST) return jsum<V, A, P + 2, false, R>(f, f[pos] - f[neg]);
+            else return jsum<V, A, P + 2, false, R>(f, (s + f[pos]) - f[neg]);
+        }
+    }
+}
+
+// density (index order, +1 last: Sec. 2.2) and the alternating-sign momentum
+// sums over opposite pairs (Sec. 2.2, e.g. u_x = f1 - f2 + f7 - f8 + ...)
+template <class V, class R>
+__device__ __forceinline__ void moments(const R* f, R& rho, R* j) {
+    rho = f[0];
+    static_for<1, V::Q>([&](auto I) { rho = rho + f[I.value]; });
+    rho = rho + R(1);
+    j[0] = jsum<V, 0, 1, true, R>(f, R(0));
+    j[1] = jsum<V, 1, 1, true, R>(f, R(0));
+    j[2] = jsum<V, 2, 1, true, R>(f, R(0));
+}
+
+// u = (j + F/2) / rho (Guo), before clamping
+template <class R>
+__device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = (k.force ? fmaR(R(0.5), k.F[a], j[a]) : j[a]) / rho;
+}
+
+// Shifted equilibrium with three FMAs per population (footnote of Sec. 2.2):
+// f^eq-s = A (0.5 (B^2 + C) +- B) + D, A = w rho, B = 3 u.c, C = -3 u.u, D = w (rho - 1).
+// Bp receives B of the first member of every pair.
+template <class V, class R>
+__device__ __forceinline__ void equilibrium(R rho, const R* u, R* feq, R* Bp) {
+    R t = u[0] * u[0];
+    t = t + u[1] * u[1];
+    if constexpr (V::D == 3) t = t + u[2] * u[2];
+    const R C = R(-3) * t;
+    const R u3[3] = {R(3) * u[0], R(3) * u[1], R(3) * u[2]};
+    const R rhom1 = rho - R(1);
+    const R w0 = R(V::w(0));
+    feq[0] = fmaR(w0 * rho, R(0.5) * C, w0 * rhom1);
+    static_for<0, (V::Q - 1) / 2>([&](auto K) {
+        constexpr int p = 2 * K.value + 1;
+        const R w = R(V::w(p));
+        const R A = w * rho, D = w * rhom1;
+        const R B = csum<V, p, R>(u3);
+        const R X = fmaR(B, B, C);
+        feq[p] = fmaR(A, fmaR(R(0.5), X, B), D);
+        feq[p + 1] = fmaR(A, fmaR(R(0.5), X, -B), D);
+        Bp[p] = B;
+    });
+}
+
+// Guo source S_i = 3 w_i ((c_i.F - u.F) + B_i (c_i.F)) with B_i = 3 c_i.u
+template <class V, class R>
+__device__ __forceinline__ void guo_source(const Relax<R>& k, const R* u, const R* Bp, R* S) {
+    R uF = u[0] * k.F[0];
+    uF = fmaR(u[1], k.F[1], uF);
+    if constexpr (V::D == 3) uF = fmaR(u[2], k.F[2], uF);
+    S[0] = R(3.0 * V::w(0)) * (-uF);
+    static_for<0, (V::Q - 1) / 2>([&](auto K) {
+        constexpr int p = 2 * K.value + 1;
+        const R cF = csum<V, p, R>(k.F);
+        const R w3 = R(3.0 * V::w(p));
+        S[p] = w3 * fmaR(Bp[p], cF, cF - uF);
+        S[p + 1] = w3 * fmaR(Bp[p], cF, (-cF) - uF);
+    });
+}
+
+// streamed populations f -> post-collision populations (in place)
+template <class V, int COLL, class R>
+__device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
+    R rho, j[3], u[3];
+    moments<V, R>(f, rho, j);
+    velocity<R>(k, rho, j, u);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = minR(maxR(u[a], -k.cs), k.cs);
+    R feq[V::Q], Bp[V::Q], S[V::Q];
+    equilibrium<V, R>(rho, u, feq, Bp);
+    if (k.force) guo_source<V, R>(k, u, Bp, S);
+    if constexpr (COLL == 0) {   // SRT: fma(1 - omega, f, omega f^eq)
+        if (k.force) {
+            static_for<0, V::Q>([&](auto I) {
+                constexpr int i = I.value;
+                f[i] = fmaR(k.c1, f[i], fmaR(k.om, feq[i], k.cSp * S[i]));
+            });
+        } else {
+            static_for<0, V::Q>([&](auto I) {
+                constexpr int i = I.value;
+                f[i] = fmaR(k.c1, f[i], k.om * feq[i]);
+            });
+        }
+    } else {                     // TRT on the symmetric / antisymmetric parts of each pair
+        const R a0 = f[0] - feq[0];
+        f[0] = fmaR(-k.omp, a0, k.force ? fmaR(k.cSp, S[0], f[0]) : f[0]);
+        static_for<0, (V::Q - 1) / 2>([&](auto K) {
+            constexpr int p = 2 * K.value + 1, q = p + 1;
+            const R a = f[p] - feq[p], b = f[q] - feq[q];
+            const R sp = R(0.5) * (a + b), sm = R(0.5) * (a - b);
+            R fp = f[p], fq = f[q];
+            if (k.force) {
+                const R Sp = R(0.5) * (S[p] + S[q]), Sm = R(0.5) * (S[p] - S[q]);
+                fp = fp + fmaR(k.cSm, Sm, k.cSp * Sp);
+                fq = fq + fmaR(-k.cSm, Sm, k.cSp * Sp);
+            }
+            f[p] = fmaR(-k.omm, sm, fmaR(-k.omp, sp, fp));
+            f[q] = fmaR(k.omm, sm, fmaR(-k.omp, sp, fq));
+        });
+    }
+}
+
+template <class V, class R>
+__device__ __forceinline__ void equilibrium_only(R rho, const R* u, R* feq) {
+    R Bp[V::Q];
+    equilibrium<V, R>(rho, u, feq, Bp);
+}
+
+}  // namespace lbm

@@ -1,0 +1,262 @@
+// Ensembles: many independent lattices of uneven size advanced by ONE kernel
+// launch per time step.  The members' cells are cut into thread-block tiles
+// (bx x by cells of one xy-plane); a prefix-sum table maps a block index to
+// its member and tile, and a device table holds each member's pointers,
+// sizes and relaxation constants.  Steps are replayed from a CUDA graph of
+// kGraphSteps launches.  Every cell runs the same per-cell routine as the
+// single-lattice kernel, so results are bit-for-bit those of one launch per
+// member.
+#include <cmath>
+#include <type_traits>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_handle.h"
+
+using namespace lbm;
+
+namespace {
+constexpr int kGraphSteps = 64;
+}
+
+struct lbm_ensemble {
+    std::vector<lbm_handle*> m;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;
+    KernelSet* ks = nullptr;
+    bool fp64 = false, aa = false;
+    void* table = nullptr;          // EnsMember<R>[count]
+    int* tile_start = nullptr;      // count + 1
+    int total_tiles = 0;
+    int bx = 32, by = 8;
+    int64_t s = 0;                  // steps taken through the ensemble
+    std::vector<int64_t> t0;        // member step counters at creation
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::string err;
+
+    lbm_status cuda(cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return LBM_OK;
+        err = std::string(what) + ": " + cudaGetErrorString(e);
+        return LBM_ERR_CUDA;
+    }
+    void drop_graphs() {
+        for (auto& g : graph)
+            if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    }
+};
+
+namespace {
+
+template <class R>
+std::vector<EnsMember<R>> make_table(lbm_ensemble* e, std::vector<int>& starts) {
+    std::vector<EnsMember<R>> tab(e->m.size());
+    starts.assign(e->m.size() + 1, 0);
+    long long total = 0;
+    for (size_t k = 0; k < e->m.size(); ++k) {
+        lbm_handle* h = e->m[k];
+        const Relax<R>* rk_ptr;
+        if constexpr (std::is_same<R, double>::value) rk_ptr = &h->kd; else rk_ptr = &h->kf;
+        const Relax<R>& rk = *rk_ptr;
+        EnsMember<R>& M = tab[k];
+        M.args[0] = h->args(rk, e->aa ? 0 : h->cur);
+        M.args[1] = h->args(rk, e->aa ? 0 : 1 - h->cur);
+        M.tiles_x = (h->p.nx + e->bx - 1) / e->bx;
+        M.tiles_y = (h->p.ny + e->by - 1) / e->by;
+        starts[k] = (int)total;
+        total += (long long)M.tiles_x * M.tiles_y * h->p.nz;
+    }
+    starts[e->m.size()] = (int)total;
+    e->total_tiles = (int)total;
+    return tab;
+}
+
+lbm_status upload_table(lbm_ensemble* e) {
+    std::vector<int> starts;
+    size_t bytes;
+    const void* src;
+    std::vector<EnsMember<float>> tf;
+    std::vector<EnsMember<double>> td;
+    if (e->fp64) { td = make_table<double>(e, starts); src = td.data(); bytes = td.size() * sizeof(EnsMember<double>); }
+    else { tf = make_table<float>(e, starts); src = tf.data(); bytes = tf.size() * sizeof(EnsMember<float>); }
+    if (!e->table) {
+        if (e->cuda(cudaMalloc(&e->table, bytes), "table alloc")) return LBM_ERR_OOM;
+        if (e->cuda(cudaMalloc((void**)&e->tile_start, starts.size() * sizeof(int)), "table alloc")) return LBM_ERR_OOM;
+    }
+    if (e->cuda(cudaMemcpyAsync(e->table, src, bytes, cudaMemcpyHostToDevice, e->stream), "table upload"))
+        return LBM_ERR_CUDA;
+    if (e->cuda(cudaMemcpyAsync(e->tile_start, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                e->stream), "table upload"))
+        return LBM_ERR_CUDA;
+    if (e->cuda(cudaStreamSynchronize(e->stream), "sync")) return LBM_ERR_CUDA;
+    e->drop_graphs();
+    return LBM_OK;
+}
+
+// kernel launch of ensemble step number `s` (0-based since creation)
+lbm_status launch(lbm_ensemble* e, int64_t s, cudaStream_t stream) {
+    Launch L;
+    L.block = dim3(e->bx, e->by, 1);
+    L.grid = dim3(e->total_tiles, 1, 1);
+    L.stream = stream;
+    const int64_t t = e->t0[0] + s;
+    const int scheme = !e->aa ? SCHEME_AB : ((t & 1) ? SCHEME_AA_LOC : SCHEME_AA_PP);
+    const int parity = e->aa ? 0 : (int)(s & 1);
+    return e->cuda(e->ks->ens[scheme](e->table, e->tile_start, (int)e->m.size(), parity, L), "ensemble kernel");
+}
+
+lbm_status check_members(lbm_ensemble* e) {
+    for (size_t k = 0; k < e->m.size(); ++k) {
+        if (e->m[k]->sticky) return LBM_ERR_STATE;
+        if (e->m[k]->t != e->t0[k] + e->s) {
+            e->err = "a member was stepped or re-initialised outside the ensemble; create a new ensemble";
+            return LBM_ERR_STATE;
+        }
+    }
+    return LBM_OK;
+}
+
+void advance_members(lbm_ensemble* e, int64_t n) {
+    for (lbm_handle* h : e->m) {
+        h->t += n;
+        if (!h->aa() && (n & 1)) h->cur ^= 1;
+    }
+    e->s += n;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out) {
+    if (!members || count < 1 || !out) return LBM_ERR_ARG;
+    *out = nullptr;
+    lbm_handle* h0 = members[0];
+    if (!h0 || h0->p.velset != LBM_D3Q19) return LBM_ERR_UNSUPPORTED;
+    long long tiles_bound = 0;
+    for (int k = 0; k < count; ++k) {
+        lbm_handle* h = members[k];
+        if (!h) return LBM_ERR_ARG;
+        if (h->sticky) return LBM_ERR_STATE;
+        if (h->p.velset != h0->p.velset || h->p.collision != h0->p.collision || h->p.storage != h0->p.storage ||
+            h->p.arith != h0->p.arith || h->p.scheme != h0->p.scheme || !h->flags || (h->t & 1) != (h0->t & 1))
+            return LBM_ERR_ARG;
+        for (int j = 0; j < k; ++j)
+            if (members[j] == h) return LBM_ERR_ARG;
+        tiles_bound += (long long)h->N;   // at least one cell per tile
+    }
+    if (tiles_bound > 0x7FFFFFFFll) return LBM_ERR_UNSUPPORTED;
+    lbm_ensemble* e = new lbm_ensemble;
+    e->m.assign(members, members + count);
+    e->stream = h0->stream;
+    e->ks = h0->ks;
+    e->fp64 = h0->fp64();
+    e->aa = h0->aa();
+    for (lbm_handle* h : e->m) e->t0.push_back(h->t);
+    if (cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking) != cudaSuccess) {
+        delete e;
+        return LBM_ERR_CUDA;
+    }
+    const lbm_status st = upload_table(e);
+    if (st != LBM_OK) {
+        lbm_ensemble_destroy(e);
+        return st;
+    }
+    *out = e;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_ensemble_destroy(lbm_ensemble* e) {
+    if (!e) return LBM_OK;
+    cudaStreamSynchronize(e->stream);
+    e->drop_graphs();
+    if (e->table) cudaFree(e->table);
+    if (e->tile_start) cudaFree(e->tile_start);
+    if (e->capture) cudaStreamDestroy(e->capture);
+    delete e;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps) {
+    if (!e || nsteps < 0) return LBM_ERR_ARG;
+    lbm_status st = check_members(e);
+    if (st != LBM_OK) return st;
+    int64_t done = 0;
+    while (nsteps - done >= kGraphSteps) {
+        const int key = (int)((e->aa ? e->t0[0] + e->s : e->s) & 1);
+        if (!e->graph[key]) {
+            cudaGraph_t g = nullptr;
+            if (e->cuda(cudaStreamBeginCapture(e->capture, cudaStreamCaptureModeThreadLocal), "capture")) return LBM_ERR_CUDA;
+            lbm_status cst = LBM_OK;
+            for (int k = 0; k < kGraphSteps && cst == LBM_OK; ++k) cst = launch(e, e->s + k, e->capture);
+            const cudaError_t ce = cudaStreamEndCapture(e->capture, &g);
+            if (cst != LBM_OK) { if (g) cudaGraphDestroy(g); return cst; }
+            if (e->cuda(ce, "end capture")) return LBM_ERR_CUDA;
+            const cudaError_t ie = cudaGraphInstantiate(&e->graph[key], g, 0);
+            cudaGraphDestroy(g);
+            if (e->cuda(ie, "graph instantiate")) return LBM_ERR_CUDA;
+        }
+        if (e->cuda(cudaGraphLaunch(e->graph[key], e->stream), "graph launch")) return LBM_ERR_CUDA;
+        advance_members(e, kGraphSteps);
+        done += kGraphSteps;
+    }
+    for (; done < nsteps; ++done) {
+        st = launch(e, e->s, e->stream);
+        if (st != LBM_OK) return st;
+        advance_members(e, 1);
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps) {
+    if (!e || nsteps < 0) return LBM_ERR_ARG;
+    lbm_status st = check_members(e);
+    if (st != LBM_OK) return st;
+    for (int64_t k = 0; k < nsteps; ++k) {
+        for (lbm_handle* h : e->m) {
+            st = lbm_internal_step(h, e->stream);   // advances h's counters
+            if (st != LBM_OK) return st;
+        }
+        e->s += 1;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by) {
+    if (!e || bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32 != 0) return LBM_ERR_ARG;
+    lbm_status st = check_members(e);
+    if (st != LBM_OK) return st;
+    e->bx = bx;
+    e->by = by;
+    return upload_table(e);
+}
+
+extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx_out, int* by_out) {
+    if (!e || trial_steps < 1) return LBM_ERR_ARG;
+    static const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {16, 16}, {32, 4}, {64, 2}, {16, 8}, {128, 1}};
+    float best = INFINITY;
+    int bb[2] = {e->bx, e->by};
+    cudaEvent_t ev[2];
+    if (e->cuda(cudaEventCreate(&ev[0]), "event") || e->cuda(cudaEventCreate(&ev[1]), "event")) return LBM_ERR_CUDA;
+    lbm_status st = LBM_OK;
+    for (const auto& sh : shapes) {
+        st = lbm_ensemble_set_block(e, sh[0], sh[1]);
+        if (st != LBM_OK) break;
+        st = lbm_ensemble_step(e, 2);   // warm-up
+        if (st != LBM_OK) break;
+        cudaEventRecord(ev[0], e->stream);
+        st = lbm_ensemble_step(e, trial_steps);
+        if (st != LBM_OK) break;
+        cudaEventRecord(ev[1], e->stream);
+        if (e->cuda(cudaEventSynchronize(ev[1]), "event sync")) { st = LBM_ERR_CUDA; break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (ms < best) { best = ms; bb[0] = sh[0]; bb[1] = sh[1]; }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (st != LBM_OK) return st;
+    st = lbm_ensemble_set_block(e, bb[0], bb[1]);
+    if (bx_out) *bx_out = bb[0];
+    if (by_out) *by_out = bb[1];
+    return st;
+}
+
+extern "C" const char* lbm_ensemble_last_error(const lbm_ensemble* e) { return e ? e->err.c_str() : "null ensemble"; }

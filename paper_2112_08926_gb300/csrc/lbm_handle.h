@@ -1,0 +1,105 @@
+// Internal state of an lbm_handle, shared by the host units of the library.
+#pragma once
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "lbm.h"
+#include "lbm_kernels.cuh"
+#include "lbm_registry.h"
+
+using lbm::KernelSet;
+using lbm::Launch;
+using lbm::Relax;
+using lbm::StepArgs;
+
+struct lbm_handle {
+    lbm_params p{};
+    int q = 0;
+    size_t N = 0;
+    int sb = 0;
+    lbm_allocator al{};
+    cudaStream_t stream = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    uint8_t* flags = nullptr;
+    float* node_u = nullptr;
+    float* node_rho = nullptr;
+    double* scratch = nullptr;
+    size_t scratch_doubles = 0;
+    double* partial = nullptr;
+    int64_t t = 0;
+    int cur = 0;
+    int bx = 128, by = 2;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+    KernelSet* ks = nullptr;
+    Relax<float> kf{};
+    Relax<double> kd{};
+    size_t device_bytes = 0;
+    std::vector<void*> allocations;
+
+    bool aa() const { return p.scheme == LBM_STREAM_AA; }
+    bool fp64() const { return p.arith == LBM_ARITH_FP64; }
+    int plane() const { return p.nx * p.ny; }
+
+    lbm_status fail(lbm_status s, const std::string& msg) {
+        if (err.empty() || s == LBM_ERR_CUDA) err = msg;
+        if (s == LBM_ERR_CUDA) sticky = s;
+        return s;
+    }
+    lbm_status cuda(cudaError_t e, const char* what) {
+        if (e == cudaSuccess) return LBM_OK;
+        return fail(LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+    void* alloc(size_t bytes) {
+        void* ptr = al.alloc(bytes, al.ctx);
+        if (ptr) {
+            allocations.push_back(ptr);
+            device_bytes += bytes;
+        }
+        return ptr;
+    }
+    void release(void*& ptr, size_t bytes) {
+        if (!ptr) return;
+        for (size_t k = 0; k < allocations.size(); ++k)
+            if (allocations[k] == ptr) { allocations.erase(allocations.begin() + k); break; }
+        al.release(ptr, al.ctx);
+        device_bytes -= bytes;
+        ptr = nullptr;
+    }
+
+    // kernel argument block for the current state
+    template <class R> StepArgs<R> args(const Relax<R>& k, int src_index) const {
+        StepArgs<R> a{};
+        a.src = f[src_index];
+        a.dst = aa() ? f[0] : f[1 - src_index];
+        a.flags = flags;
+        a.node_u = node_u;
+        a.node_rho = node_rho;
+        a.nx = p.nx; a.ny = p.ny; a.nz = p.nz;
+        a.N = (uint32_t)N;
+        a.k = k;
+        return a;
+    }
+    int scheme_now() const { return !aa() ? lbm::SCHEME_AB : ((t & 1) ? lbm::SCHEME_AA_LOC : lbm::SCHEME_AA_PP); }
+    int layout_now() const { return !aa() ? lbm::LAYOUT_AB : ((t & 1) ? lbm::LAYOUT_AA_NATURAL : lbm::LAYOUT_AA_SWAPPED); }
+    Launch step_launch(cudaStream_t s) const {
+        Launch L;
+        L.block = dim3(bx, by, 1);
+        L.grid = dim3((p.nx + bx - 1) / bx, (p.ny + by - 1) / by, p.nz);
+        L.stream = s;
+        return L;
+    }
+    int planes_per_chunk(int per_cell) const {
+        size_t per_plane = (size_t)plane() * per_cell;
+        size_t k = scratch_doubles / per_plane;
+        return (int)std::max<size_t>(1, std::min<size_t>(k, (size_t)p.nz));
+    }
+};
+
+
+// one stream-collide step of h launched on stream s (advances h's counters)
+lbm_status lbm_internal_step(lbm_handle* h, cudaStream_t s);

@@ -1,0 +1,361 @@
+// Stream-collide kernels for sm_103a (arXiv 2112.08926, appendix "LBM
+// equations in a nutshell" with DDF shifting, fused into one pass per step).
+//
+// One thread updates one cell; consecutive threads take consecutive x, so
+// every population array is read and written with coalesced warp accesses in
+// structure-of-arrays order f[i*N + n].  Neighbour indices come from three
+// wrapped offsets per axis (no integer division in the loop).  Streaming
+// schemes:
+//   AB     pull from copy A, write copy B (the paper's one-step pull, Sec. 5);
+//   AA_PP  in-place, odd half of A-A: pull each population from the
+//          opposite slot of the upstream cell, push the result into the
+//          downstream cell's slot;
+//   AA_LOC in-place, even half: read the own slots, write the opposite ones.
+// Both A-A halves touch exactly the memory they read, so one copy suffices,
+// and they give bit-for-bit the A-B result.
+#pragma once
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+enum { SCHEME_AB = 0, SCHEME_AA_PP = 1, SCHEME_AA_LOC = 2 };
+enum { LAYOUT_AB = 0, LAYOUT_AA_SWAPPED = 1, LAYOUT_AA_NATURAL = 2 };
+enum { PROBE_FIELDS = 0, PROBE_F = 1, PROBE_REDUCE = 2 };
+
+// internal flag bit set by the library: a neighbour is a moving wall
+constexpr uint32_t F_NEAR_MOVING = 0x80u;
+
+template <class R> struct StepArgs {
+    const void* src;          // A-B: copy read this step; A-A: the single copy
+    void* dst;                // A-B: copy written; A-A: same as src
+    const uint8_t* flags;     // NULL for the flag-free periodic kernel
+    const float* node_u;      // 3*N, component-major
+    const float* node_rho;    // N
+    int nx, ny, nz;
+    uint32_t N;
+    Relax<R> k;
+};
+
+struct Nbr {
+    uint32_t xo[3], yo[3], zo[3];   // wrapped offsets for delta = -1, 0, +1
+    __device__ __forceinline__ Nbr(int x, int y, int z, int nx, int ny, int nz) {
+        const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
+        xo[0] = x == 0 ? nx - 1 : x - 1;
+        xo[1] = x;
+        xo[2] = x == nx - 1 ? 0 : x + 1;
+        yo[0] = (uint32_t)(y == 0 ? ny - 1 : y - 1) * nx;
+        yo[1] = (uint32_t)y * nx;
+        yo[2] = (uint32_t)(y == ny - 1 ? 0 : y + 1) * nx;
+        zo[0] = (uint32_t)(z == 0 ? nz - 1 : z - 1) * plane;
+        zo[1] = (uint32_t)z * plane;
+        zo[2] = (uint32_t)(z == nz - 1 ? 0 : z + 1) * plane;
+    }
+    // cell x - c_i (upstream) and x + c_i (downstream)
+    template <class V, int I> __device__ __forceinline__ uint32_t up() const {
+        return xo[1 - V::c(I, 0)] + yo[1 - V::c(I, 1)] + zo[1 - V::c(I, 2)];
+    }
+    template <class V, int I> __device__ __forceinline__ uint32_t down() const {
+        return xo[1 + V::c(I, 0)] + yo[1 + V::c(I, 1)] + zo[1 + V::c(I, 2)];
+    }
+    __device__ __forceinline__ uint32_t self() const { return xo[1] + yo[1] + zo[1]; }
+};
+
+// Moving-wall term of the bounce-back (Sec. 4.4): 6 w_i rho_w (c_i . u_w),
+// rho_w = 1, u_w read at the wall cell m.
+template <class V, int I, class R>
+__device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t m) {
+    const R uw[3] = {(R)node_u[m], (R)node_u[N + m], (R)node_u[2 * N + m]};
+    return R(6.0 * V::w(I)) * csum<V, I, R>(uw);
+}
+
+// Streamed population i of the cell that streams at `nb` (A-B or the first
+// A-A half).  A solid upstream cell reflects the cell's own opposite
+// population (mid-grid bounce-back), plus the moving-wall term; a free-slip
+// upstream cell (A-B only) hands over the mirror population of the cell next
+// to it, falling back to bounce-back if that cell is solid too.
+template <class V, int FMT, class R, bool FLAGS, bool AA, int I>
+__device__ __forceinline__ R pull(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
+                                  const Nbr& nb) {
+    using S = Storage<FMT>;
+    const size_t N = a.N;
+    const uint32_t j = nb.up<V, I>();
+    constexpr int slot = AA ? opposite(I) : I;
+    if (!FLAGS) return S::template load<R>(src, (size_t)slot * N + j);
+    const uint32_t fy = a.flags[j];
+    if (!(fy & F_WALL)) return S::template load<R>(src, (size_t)slot * N + j);
+    if constexpr (!AA) {
+        if (fy & F_FREESLIP) {
+            const int axis = (fy >> 5) & 3;
+            if (axis < 3) {
+                constexpr int cx = V::c(I, 0), cy = V::c(I, 1), cz = V::c(I, 2);
+                constexpr int m0 = mirror<V>(I, 0), m1 = mirror<V>(I, 1), m2 = mirror<V>(I, 2);
+                const uint32_t j2 = nb.xo[axis == 0 ? 1 : 1 - cx] + nb.yo[axis == 1 ? 1 : 1 - cy] +
+                                    nb.zo[axis == 2 ? 1 : 1 - cz];
+                if (!(a.flags[j2] & F_WALL)) {
+                    const int mi = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
+                    return S::template load<R>(src, (size_t)mi * N + j2);
+                }
+            }
+        }
+    }
+    constexpr int bslot = AA ? I : opposite(I);
+    R v = S::template load<R>(src, (size_t)bslot * N + nb.self());
+    if (fy & F_MOVING) v = v + moving_term<V, I, R>(a.node_u, N, j);
+    return v;
+}
+
+// Streamed populations of cell n at (x,y,z) for the given memory layout.
+template <class V, int FMT, class R, bool FLAGS, int LAYOUT>
+__device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
+                                       int x, int y, int z, uint32_t n, uint32_t fl, R* f) {
+    using S = Storage<FMT>;
+    if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {
+        static_for<0, V::Q>([&](auto I) {
+            f[I.value] = S::template load<R>(src, (size_t)I.value * a.N + n);
+        });
+        if (FLAGS && (fl & F_NEAR_MOVING)) {
+            const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
+            static_for<1, V::Q>([&](auto I) {
+                const uint32_t j = nb.up<V, I.value>();
+                if (a.flags[j] & F_MOVING) f[I.value] = f[I.value] + moving_term<V, I.value, R>(a.node_u, a.N, j);
+            });
+        }
+    } else {
+        int sx = x;
+        if (FLAGS && LAYOUT == LAYOUT_AB && (fl & F_OUTFLOW)) sx = x == 0 ? a.nx - 1 : x - 1;
+        const Nbr nb(sx, y, z, a.nx, a.ny, a.nz);
+        static_for<0, V::Q>([&](auto I) {
+            f[I.value] = pull<V, FMT, R, FLAGS, LAYOUT == LAYOUT_AA_SWAPPED, I.value>(a, src, nb);
+        });
+    }
+}
+
+// One fused stream-collide update of cell (x, y, z).
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS>
+__device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, int z) {
+    using S = Storage<FMT>;
+    using T = typename S::T;
+    const size_t N = a.N;
+    const uint32_t n = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
+    const T* src = (const T*)a.src;
+    T* dst = (T*)a.dst;
+    uint32_t fl = 0;
+    if (FLAGS) {
+        fl = a.flags[n];
+        if (fl & F_WALL) return;
+    }
+    R f[V::Q];
+    if (FLAGS && (fl & F_EQ)) {
+        const R u[3] = {(R)a.node_u[n], (R)a.node_u[N + n], (R)a.node_u[2 * N + n]};
+        equilibrium_only<V, R>((R)a.node_rho[n], u, f);
+    } else {
+        constexpr int LAYOUT = SCHEME == SCHEME_AB ? LAYOUT_AB
+                             : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
+        gather<V, FMT, R, FLAGS, LAYOUT>(a, src, x, y, z, n, fl, f);
+        collide<V, COLL, R>(a.k, f);
+    }
+    if constexpr (SCHEME == SCHEME_AB) {
+        static_for<0, V::Q>([&](auto I) { S::template store<R>(dst, (size_t)I.value * N + n, f[I.value]); });
+    } else if constexpr (SCHEME == SCHEME_AA_LOC) {
+        static_for<0, V::Q>([&](auto I) {
+            S::template store<R>(dst, (size_t)opposite(I.value) * N + n, f[I.value]);
+        });
+    } else {
+        const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
+        static_for<0, V::Q>([&](auto I) {
+            constexpr int i = I.value;
+            const uint32_t d = nb.down<V, i>();
+            if (FLAGS && (a.flags[d] & F_WALL))   // reflected back into this cell
+                S::template store<R>(dst, (size_t)opposite(i) * N + n, f[i]);
+            else
+                S::template store<R>(dst, (size_t)i * N + d, f[i]);
+        });
+    }
+}
+
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS>
+__global__ void __launch_bounds__(256) k_step(const StepArgs<R> a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    cell_step<V, COLL, FMT, R, SCHEME, FLAGS>(a, x, y, (int)blockIdx.z);
+}
+
+// ---------------------------------------------------------------- ensemble
+// Many independent lattices in one launch.  Each member's cells are cut into
+// tiles of bx*by cells in one xy-plane; tile_start[m] is the first global
+// tile of member m (prefix sum, tile_start[count] = total).  A block finds
+// its member by binary search and updates one tile.
+template <class R> struct EnsMember {
+    StepArgs<R> args[2];       // args[p]: arguments for a step of parity p
+    int tiles_x, tiles_y;
+};
+
+template <class V, int COLL, int FMT, class R, int SCHEME>
+__global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __restrict__ members,
+                                                        const int* __restrict__ tile_start, int count,
+                                                        int parity) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_start + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    const EnsMember<R>& M = members[lo];
+    const int t = b - __ldg(tile_start + lo);
+    const int txy = M.tiles_x * M.tiles_y;
+    const int z = t / txy;
+    const int r = t - z * txy;
+    const int ty = r / M.tiles_x;
+    const int tx = r - ty * M.tiles_x;
+    const StepArgs<R> a = M.args[parity];
+    const int x = tx * blockDim.x + threadIdx.x;
+    const int y = ty * blockDim.y + threadIdx.y;
+    if (x >= a.nx || y >= a.ny) return;
+    cell_step<V, COLL, FMT, R, SCHEME, true>(a, x, y, z);
+}
+
+// ---------------------------------------------------------------- probes
+// Per-cell quantities from the streamed populations: fields (rho, u with the
+// Guo half-force), the populations themselves, or FP64 mass / energy sums.
+template <class R> struct ProbeArgs {
+    StepArgs<R> a;
+    int z0, z1;               // z-range handled by this launch
+    double* out;              // FIELDS: 4 x count doubles; F: q x count doubles
+    double* partial;          // REDUCE: 2 doubles per block
+};
+
+template <class V, int FMT, class R, int LAYOUT>
+__global__ void __launch_bounds__(256) k_probe(const ProbeArgs<R> p, int mode) {
+    const StepArgs<R>& a = p.a;
+    const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
+    const uint32_t count = plane * (uint32_t)(p.z1 - p.z0);
+    double m_acc = 0.0, e_acc = 0.0;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const int z = p.z0 + (int)(t / plane);
+        const uint32_t r = t - (uint32_t)(z - p.z0) * plane;
+        const int y = (int)(r / (uint32_t)a.nx);
+        const int x = (int)(r - (uint32_t)y * a.nx);
+        const uint32_t n = (uint32_t)z * plane + r;
+        const uint32_t fl = a.flags ? a.flags[n] : 0u;
+        const bool solid = fl & F_WALL;
+        R f[V::Q];
+        if (!solid) {
+            if (a.flags) gather<V, FMT, R, true, LAYOUT>(a, (const typename Storage<FMT>::T*)a.src, x, y, z, n, fl, f);
+            else gather<V, FMT, R, false, LAYOUT>(a, (const typename Storage<FMT>::T*)a.src, x, y, z, n, fl, f);
+        }
+        if (mode == PROBE_F) {
+            static_for<0, V::Q>([&](auto I) {
+                p.out[(size_t)I.value * count + t] = solid ? 0.0 : (double)f[I.value];
+            });
+            continue;
+        }
+        double rho = 1.0, u[3] = {0.0, 0.0, 0.0};
+        if (solid) {
+        } else if (fl & F_EQ) {
+            rho = (double)a.node_rho[n];
+            for (int d = 0; d < 3; ++d) u[d] = (double)a.node_u[(size_t)d * a.N + n];
+        } else {
+            R rr, j[3], uu[3];
+            moments<V, R>(f, rr, j);
+            velocity<R>(a.k, rr, j, uu);
+            rho = (double)rr;
+            for (int d = 0; d < 3; ++d) u[d] = (double)uu[d];
+        }
+        if (mode == PROBE_FIELDS) {
+            p.out[t] = rho;
+            p.out[(size_t)count + t] = u[0];
+            p.out[2 * (size_t)count + t] = u[1];
+            p.out[3 * (size_t)count + t] = u[2];
+        } else if (!solid) {
+            m_acc += rho;
+            e_acc += 0.5 * rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        }
+    }
+    if (mode != PROBE_REDUCE) return;
+    // block reduction in FP64 (fixed order: deterministic)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m_acc += __shfl_down_sync(0xffffffffu, m_acc, o);
+        e_acc += __shfl_down_sync(0xffffffffu, e_acc, o);
+    }
+    __shared__ double sm[2][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { sm[0][warp] = m_acc; sm[1][warp] = e_acc; }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        m_acc = lane < nw ? sm[0][lane] : 0.0;
+        e_acc = lane < nw ? sm[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            m_acc += __shfl_down_sync(0xffffffffu, m_acc, o);
+            e_acc += __shfl_down_sync(0xffffffffu, e_acc, o);
+        }
+        if (lane == 0) {
+            p.partial[2 * blockIdx.x] = m_acc;
+            p.partial[2 * blockIdx.x + 1] = e_acc;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- put
+// Initial populations for cells of planes z0..z1-1 from device doubles:
+// INIT: shifted equilibrium (Sec. 2.2) of (rho, ux, uy, uz), each `count`
+// doubles or NULL (rho = 1, u = 0); SETF: post-collision populations in[0]
+// (q x count doubles).  Solid cells get zero.  A-A stores in the swapped
+// layout (slot opposite(i)).
+template <class R> struct PutArgs {
+    StepArgs<R> a;
+    int z0, z1;
+    const double* in[4];
+};
+
+template <class V, int FMT, class R, bool AA>
+__global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
+    using S = Storage<FMT>;
+    const StepArgs<R>& a = p.a;
+    const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
+    const uint32_t count = plane * (uint32_t)(p.z1 - p.z0);
+    typename S::T* dst = (typename S::T*)a.dst;
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const uint32_t n = (uint32_t)p.z0 * plane + t;
+        const bool solid = a.flags && (a.flags[n] & F_WALL);
+        R f[V::Q];
+        if (setf) {
+            static_for<0, V::Q>([&](auto I) { f[I.value] = (R)p.in[0][(size_t)I.value * count + t]; });
+        } else {
+            const R rho = p.in[0] ? (R)p.in[0][t] : R(1);
+            const R u[3] = {p.in[1] ? (R)p.in[1][t] : R(0), p.in[2] ? (R)p.in[2][t] : R(0),
+                            (V::D == 3 && p.in[3]) ? (R)p.in[3][t] : R(0)};
+            equilibrium_only<V, R>(rho, u, f);
+        }
+        static_for<0, V::Q>([&](auto I) {
+            constexpr int slot = AA ? opposite(I.value) : I.value;
+            S::template store<R>(dst, (size_t)slot * a.N + n, solid ? R(0) : f[I.value]);
+        });
+    }
+}
+
+// Marks cells next to a moving wall (internal bit F_NEAR_MOVING), so the
+// in-place scheme adds the moving-wall term where it reads a reflected population.
+template <class V>
+__global__ void k_mark_near_moving(uint8_t* flags, int nx, int ny, int nz) {
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
+    const uint32_t N = plane * (uint32_t)nz;
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const uint32_t fl = flags[n];
+        if (fl & F_WALL) continue;
+        const int z = (int)(n / plane);
+        const uint32_t r = n - (uint32_t)z * plane;
+        const int y = (int)(r / (uint32_t)nx);
+        const int x = (int)(r - (uint32_t)y * nx);
+        const Nbr nb(x, y, z, nx, ny, nz);
+        bool near = false;
+        static_for<1, V::Q>([&](auto I) { near = near || (flags[nb.up<V, I.value>()] & F_MOVING); });
+        if (near) flags[n] = (uint8_t)(fl | F_NEAR_MOVING);
+    }
+}
+
+}  // namespace lbm

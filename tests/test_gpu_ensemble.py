@@ -1,0 +1,74 @@
+"""Ensembles: one launch per step over many uneven lattices must give exactly
+the result of one launch per member (same per-cell routine), and members
+must match the CPU oracle bit for bit (FP32 arithmetic, FP16S storage)."""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def make_members(specs, storage, scheme, P):
+    out = []
+    for s in specs:
+        g = P.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", storage, "FP32", scheme, tau=s.tau)
+        flags, node_u = W.cavity(s.n, s.u_lid)
+        g.set_geometry(flags, node_u)
+        g.set_rho_u()
+        out.append(g)
+    return out
+
+
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+def test_ensemble_equals_per_member_launches(scheme):
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=7, n_min=6, n_max=21)
+    a = make_members(specs, "FP16S", scheme, P)
+    b = make_members(specs, "FP16S", scheme, P)
+    ea, eb = P.Ensemble(a), P.Ensemble(b)
+    ea.step(150)          # two graph replays of 64 steps and 22 single launches
+    eb.step_each(150)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
+    ea.set_block(64, 4)
+    ea.step(3)
+    eb.step_each(3)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
+
+
+def test_ensemble_members_match_oracle():
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=3, n_min=5, n_max=12, seed=99)
+    mem = make_members(specs, "FP16S", "AB", P)
+    e = P.Ensemble(mem)
+    e.step(70)
+    for s, g in zip(specs, mem):
+        o = oracle.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", "ORD32", "FP16S", tau=s.tau)
+        flags, node_u = W.cavity(s.n, s.u_lid)
+        o.set_geometry(flags, node_u)
+        o.set_rho_u()
+        o.step(70)
+        assert np.array_equal(g.f(), o.f())
+
+
+def test_member_stepped_outside_is_detected():
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=2, n_min=5, n_max=8)
+    mem = make_members(specs, "FP32", "AB", P)
+    e = P.Ensemble(mem)
+    mem[0].step(1)
+    with pytest.raises(P.LBMError) as ei:
+        e.step(1)
+    assert ei.value.status == 7

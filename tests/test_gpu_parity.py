@@ -1,0 +1,204 @@
+"""GPU parity: the CUDA stream-collide path against the CPU oracle.
+
+Bar: FP32 arithmetic (every storage format) is bit-for-bit the oracle's FP32
+arithmetic in the paper's operation order (Sec. 2.2), because both sides
+round the same operations in the same order and the codecs are bit-exact.
+FP64 arithmetic with FP64 storage is within a relative L2 of 1e-12 of the
+FP64 textbook definition.  Lattices span several thread blocks with ragged
+edges; geometries mix every cell kind.
+"""
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def P():
+    import paper_2112_08926_gb300 as pkg
+    return pkg
+
+
+SHAPES = {"D2Q9": (1, 27, 45), "D3Q19": (7, 19, 37), "D3Q27": (5, 11, 35)}
+FORCE = {"D2Q9": (1e-5, -2e-5, 0.0), "D3Q19": (1e-5, -2e-5, 3e-5), "D3Q27": (-1e-5, 2e-5, 1e-5)}
+ALL_STORAGE = ["FP64", "FP32", "FP16", "FP16S", "FP16C", "P16_0S", "P16_1S", "P16_2C", "P16_0", "P16_1"]
+
+
+def geometry(vs, scheme, seed):
+    shape = SHAPES[vs]
+    if scheme == "AA":
+        return W.random_geometry(shape, seed, outflow=0.0, freeslip_frac=0.0)
+    return W.random_geometry(shape, seed)
+
+
+def run_gpu(vs, coll, storage, arith, scheme, steps, force, geo, fields, tau=0.66, block=(32, 8)):
+    nz, ny, nx = SHAPES[vs]
+    g = P().Lattice(nx, ny, nz, vs, coll, storage, arith, scheme, tau=tau, trt_lambda=0.2, force=force)
+    g.set_block(*block)
+    g.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    g.step(steps)
+    out = g.f(), g.rho_u(), g.reduce()
+    g.close()
+    return out
+
+
+def run_oracle(vs, coll, arith, storage, steps, force, geo, fields, tau=0.66):
+    nz, ny, nx = SHAPES[vs]
+    o = oracle.Lattice(nx, ny, nz, vs, coll, arith, storage, tau=tau, trt_lambda=0.2, force=force)
+    o.set_geometry(*geo)
+    o.set_rho_u(*fields)
+    o.step(steps)
+    return o.f(), o.rho_u(), o.reduce()
+
+
+@pytest.mark.parametrize("vs", ["D2Q9", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+@pytest.mark.parametrize("storage", ALL_STORAGE)
+def test_fp32_arithmetic_bitwise(vs, coll, scheme, storage):
+    geo = geometry(vs, scheme, 11)
+    fields = W.random_fields(SHAPES[vs], 12)
+    force = FORCE[vs] if storage in ("FP32", "FP16C", "P16_1S") else (0.0, 0.0, 0.0)
+    steps = 21 if scheme == "AA" else 20      # AA: odd count ends on the natural layout
+    gf, grho, gred = run_gpu(vs, coll, storage, "FP32", scheme, steps, force, geo, fields)
+    of, orho, ored = run_oracle(vs, coll, "ORD32", storage, steps, force, geo, fields)
+    assert np.array_equal(gf, of), f"max |diff| {np.abs(gf - of).max():.3e}"
+    for a, b in zip(grho, orho):
+        assert np.array_equal(a, b)
+    assert gred[0] == pytest.approx(ored[0], rel=1e-13)
+    assert gred[1] == pytest.approx(ored[1], rel=1e-11, abs=1e-300)
+
+
+@pytest.mark.parametrize("vs", ["D2Q9", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+def test_fp64_tier_matches_definition(vs, coll, scheme):
+    geo = geometry(vs, scheme, 21)
+    fields = W.random_fields(SHAPES[vs], 22)
+    gf, grho, gred = run_gpu(vs, coll, "FP64", "FP64", scheme, 30, FORCE[vs], geo, fields)
+    of, orho, ored = run_oracle(vs, coll, "DEF64", "FP64", 30, FORCE[vs], geo, fields)
+    assert np.linalg.norm(gf - of) / np.linalg.norm(of) < 1e-12
+    for a, b in zip(grho[1:], orho[1:]):
+        assert np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300) < 1e-12
+    assert gred[0] == pytest.approx(ored[0], rel=1e-13)
+
+
+@pytest.mark.parametrize("storage", ["FP64", "FP32"])
+def test_fp64_arithmetic_bitwise_against_ordered_fp64(storage):
+    vs, coll = "D3Q19", "SRT"
+    geo = geometry(vs, "AB", 31)
+    fields = W.random_fields(SHAPES[vs], 32)
+    gf, _, _ = run_gpu(vs, coll, storage, "FP64", "AB", 15, FORCE[vs], geo, fields)
+    of, _, _ = run_oracle(vs, coll, "ORD64", storage, 15, FORCE[vs], geo, fields)
+    assert np.array_equal(gf, of)
+
+
+@pytest.mark.parametrize("storage", ["FP32", "FP16S", "P16_2C"])
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+def test_flag_free_periodic_kernel(storage, scheme):
+    vs = "D3Q19"
+    nz, ny, nx = 9, 17, 70
+    fields = W.random_fields((nz, ny, nx), 5)
+    g = P().Lattice(nx, ny, nz, vs, "SRT", storage, "FP32", scheme, tau=0.53)
+    g.set_rho_u(*fields)
+    g.step(13)
+    o = oracle.Lattice(nx, ny, nz, vs, "SRT", "ORD32", storage, tau=0.53)
+    o.set_rho_u(*fields)
+    o.step(13)
+    assert np.array_equal(g.f(), o.f())
+    assert g.info().has_flags == 0
+
+
+@pytest.mark.parametrize("shape,block", [
+    ((1, 1, 1), (32, 1)), ((1, 1, 33), (32, 1)), ((3, 2, 1), (32, 1)), ((2, 3, 129), (128, 2)),
+    ((4, 5, 6), (256, 1)), ((3, 40, 3), (32, 8)),
+])
+def test_degenerate_and_ragged_sizes(shape, block):
+    nz, ny, nx = shape
+    geo = W.random_geometry(shape, 7, outflow=0.0)
+    fields = W.random_fields(shape, 8)
+    g = P().Lattice(nx, ny, nz, "D3Q19", "TRT", "FP16C", "FP32", "AB", tau=0.9, force=(1e-5, 0, 0))
+    g.set_block(*block)
+    g.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    g.step(9)
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "TRT", "ORD32", "FP16C", tau=0.9, force=(1e-5, 0, 0))
+    o.set_geometry(*geo)
+    o.set_rho_u(*fields)
+    o.step(9)
+    assert np.array_equal(g.f(), o.f())
+
+
+def test_set_f_round_trip_and_nan_detection():
+    nz, ny, nx = 4, 5, 6
+    rng = np.random.default_rng(1)
+    f = rng.uniform(-0.01, 0.01, (19, nz, ny, nx))
+    for storage in ("FP64", "FP16S"):
+        arith = "FP64" if storage == "FP64" else "FP32"
+        g = P().Lattice(nx, ny, nz, "D3Q19", "SRT", storage, arith, "AA", tau=0.8)
+        g.set_f(f)
+        o = oracle.Lattice(nx, ny, nz, "D3Q19", "SRT", "DEF64" if storage == "FP64" else "ORD32", storage, tau=0.8)
+        o.set_f(f)
+        # a periodic lattice pulls each population from its upstream neighbour
+        assert np.array_equal(g.f(), o.f())
+        g.step(3)
+        o.step(3)
+        if storage == "FP16S":
+            assert np.array_equal(g.f(), o.f())
+    bad = f.copy()
+    bad[3, 1, 2, 3] = np.nan
+    g = P().Lattice(nx, ny, nz, "D3Q19", "SRT", "FP32", "FP32", "AB", tau=0.8)
+    g.set_f(bad)
+    g.step(2)
+    with pytest.raises(P().LBMError) as ei:
+        g.reduce()
+    assert ei.value.status == 5
+
+
+def test_unsupported_geometry_for_in_place_streaming():
+    shape = (3, 4, 5)
+    flags = np.zeros(shape, np.uint8)
+    flags[0, 0, 0] = W.OUTFLOW
+    g = P().Lattice(5, 4, 3, "D3Q19", "SRT", "FP32", "FP32", "AA", tau=0.8)
+    with pytest.raises(P().LBMError) as ei:
+        g.set_geometry(flags)
+    assert ei.value.status == 4
+    flags[0, 0, 0] = W.MOVING            # MOVING without WALL
+    with pytest.raises(P().LBMError) as ei:
+        g.set_geometry(flags)
+    assert ei.value.status == 1
+
+
+def test_autotune_keeps_results():
+    shape = (6, 13, 40)
+    geo = W.random_geometry(shape, 3, outflow=0.0, freeslip_frac=0.0)
+    fields = W.random_fields(shape, 4)
+    res = []
+    for tune in (False, True):
+        g = P().Lattice(40, 13, 6, "D3Q19", "SRT", "FP16S", "FP32", "AA", tau=0.7)
+        g.set_geometry(*geo)
+        g.set_rho_u(*fields)
+        if tune:
+            bx, by = g.autotune(trial_steps=2)
+            assert bx * by % 32 == 0
+            done = g.info().step
+        else:
+            done = 0
+        res.append((g, done))
+    g0, _ = res[0]
+    g1, done = res[1]
+    g0.step(done)
+    assert np.array_equal(g0.f(), g1.f())
