@@ -184,9 +184,10 @@ lbm_status lbm_codec_encode_bits(int storage, uint32_t first, int64_t n, uint16_
 /* ---- ensembles: many independent lattices advanced by one launch per step -- */
 typedef struct lbm_ensemble lbm_ensemble;
 
-/* Group `count` handles that share velset, collision, storage, arith and
- * scheme (LBM_ERR_ARG otherwise) and have flags set.  The members keep their
- * own data; the ensemble adds a device descriptor table and a tile list.
+/* Group `count` D3Q19 handles that share collision, storage, arith and
+ * scheme (LBM_ERR_ARG otherwise; other velocity sets LBM_ERR_UNSUPPORTED),
+ * have flags set and the same step parity.  The members keep their own data;
+ * the ensemble adds a device descriptor table and a per-tile member table.
  * All launches go to the first member's stream. */
 lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out);
 /* Advance every member nsteps steps: one launch per step over all members,
@@ -194,9 +195,10 @@ lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemb
 lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps);
 /* Same result, one launch per member per step (the baseline). */
 lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps);
-/* Tile shape of the ensemble launch (bx*by a multiple of 32, at most 256). */
+/* Cells per tile (thread block) of the ensemble launch: bx a multiple of 32
+ * in [32, 256], by must be 1 (tiles are runs of consecutive cells). */
 lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by);
-/* Times trial_steps steps for each of a fixed list of tile shapes and keeps
+/* Times trial_steps steps for each of a fixed list of tile sizes and keeps
  * the fastest.  The trial steps are real steps: every member advances by
  * (trial_steps + 2) * (number of shapes) steps.  Results do not depend on
  * the tile shape. */

@@ -33,7 +33,8 @@
  *   - where fewer exponent bits fit below the regime than the format has,
  *     the missing exponent bits read as zero; for P16_2C this includes the
  *     single bit that does fit when 13 regime zeros are present;
- *   - NaN inputs: see fp16c_from_float and the posit encoders.
+ *   - NaN inputs: see fp16c_from_float; posit encoders saturate a NaN with
+ *     the sign of the input.
  */
 #include "oracle.h"
 
@@ -246,13 +247,18 @@ float decode_value(int fmt, uint16_t c) {
     }
 }
 
+/* posit formats: a NaN saturates with the sign of the input (the scaling
+ * product of the S variants is not consulted, since hardware may return a
+ * NaN of either sign for NaN * 128) */
+uint16_t nan_code(float x) { return (uint16_t)(((fbits(x) >> 16) & 0x8000u) | 0x7FFFu); }
+
 uint16_t encode_value(int fmt, float x) {
     switch (fmt) {
     case ORC_FP16:   return fp16_from_float(x);
     case ORC_FP16S:  return fp16_from_float(x * 32768.0f);        /* FP32 product */
     case ORC_FP16C:  return fp16c_from_float(x);
-    case ORC_P16_0S: return p160_from_float(x * 128.0f);
-    case ORC_P16_1S: return p161_from_float(x * 128.0f);
+    case ORC_P16_0S: return std::isnan(x) ? nan_code(x) : p160_from_float(x * 128.0f);
+    case ORC_P16_1S: return std::isnan(x) ? nan_code(x) : p161_from_float(x * 128.0f);
     case ORC_P16_2C: return p162c_from_float(x);
     case ORC_P16_0:  return p160_from_float(x);
     case ORC_P16_1:  return p161_from_float(x);

@@ -236,11 +236,11 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
             if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
         }
     }
-    if (h->aa() && any_moving) {
+    {
         const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
-        if (h->p.velset == LBM_D2Q9) k_mark_near_moving<D2Q9><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
-        else if (h->p.velset == LBM_D3Q19) k_mark_near_moving<D3Q19><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
-        else k_mark_near_moving<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
+        if (h->p.velset == LBM_D2Q9) k_mark_neighbours<D2Q9><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
+        else if (h->p.velset == LBM_D3Q19) k_mark_neighbours<D3Q19><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
+        else k_mark_neighbours<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
         if (h->cuda(cudaGetLastError(), "mark kernel")) return LBM_ERR_CUDA;
     }
     if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;

@@ -99,23 +99,21 @@ __device__ __forceinline__ float fp16c_decode(uint32_t c) {
 }
 
 // FP32 -> FP16C: round to nearest, halfway cases away from zero, subnormals
-// kept, saturation at the largest magnitude.  Normal range: add half a unit
-// of bit 12 and drop 12 mantissa bits, re-bias the exponent by 127-15.
-// Subnormal range (|x| < 2^-14): the 24-bit significand shifted to units of
-// 2^-25 with a final round-half-up shift.  NaN patterns whose rounding
-// increment would carry into the sign give a zero of the opposite sign.
+// kept, saturation at the largest magnitude.  |x| * 2^-112 (rounded toward
+// zero) puts the FP16C exponent range onto FP32 exponents 1..15 and the FP16C
+// subnormals onto FP32 subnormals, truncated to whole units of 2^-149 = 2^-37
+// in FP16C terms; adding half a unit of bit 12 and dropping 12 bits then
+// rounds half up in both ranges at once (the truncation cannot move a value
+// across a halfway point, which lies on the 2^-149 grid).  NaN patterns whose
+// rounding increment would carry into the sign give a zero of the opposite
+// sign.
 __device__ __forceinline__ uint32_t fp16c_encode(float x) {
     const uint32_t b = u32(x);
-    const uint32_t s = (b >> 16) & 0x8000u;
     const uint32_t a = b & 0x7FFFFFFFu;
-    const uint32_t norm = min(((a + 0x800u) >> 12) - (112u << 11), 0x7FFFu);
-    const uint32_t E = a >> 23;
-    const uint32_t M = (a & 0x7FFFFFu) | 0x800000u;
-    const uint32_t sh = min(124u - min(E, 124u), 31u);
-    const uint32_t den = ((M >> sh) + 1u) >> 1;
-    uint32_t r = s | (a < 0x38800000u ? den : norm);
-    if (a >= 0x7FFFF800u) r = s ^ 0x8000u;
-    return r;
+    const float y = __fmul_rz(__uint_as_float(a), 0x1p-112f);
+    const uint32_t code = min((u32(y) + 0x800u) >> 12, 0x7FFFu);
+    const uint32_t s = (b >> 16) & 0x8000u;
+    return a >= 0x7FFFF800u ? (s ^ 0x8000u) : (s | code);
 }
 
 // length of the regime run of a 15-bit posit magnitude (bits 14..0):
@@ -233,46 +231,85 @@ __device__ __forceinline__ uint32_t p162c_encode(float x) {
     return s | mag;
 }
 
+// Codec16<FMT>: dec/enc convert between a code and the population value;
+// dec_g/enc_g work on the value times 2^SL, the scale the S formats apply
+// before encoding (Sec. 3.1.3, 3.2.2), so a kernel that keeps its populations
+// scaled skips both multiplications.  Scaling by a power of two commutes with
+// rounding, so either route gives the same codes.
 template <int FMT> struct Codec16;
 template <> struct Codec16<2> {   // FP16: IEEE binary16, round to nearest even (hardware)
-    __device__ static float dec(uint32_t c) { return __half2float(__ushort_as_half((unsigned short)c)); }
-    __device__ static uint32_t enc(float x) { return __half_as_ushort(__float2half_rn(x)); }
+    static constexpr int SL = 0;
+    __device__ static float dec_g(uint32_t c) { return __half2float(__ushort_as_half((unsigned short)c)); }
+    __device__ static uint32_t enc_g(float g) { return __half_as_ushort(__float2half_rn(g)); }
+    __device__ static float dec(uint32_t c) { return dec_g(c); }
+    __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
 template <> struct Codec16<3> {   // FP16S: binary16 of x * 2^15 (Sec. 3.1.3)
-    __device__ static float dec(uint32_t c) {
-        return __half2float(__ushort_as_half((unsigned short)c)) * 3.0517578125e-5f;
-    }
-    __device__ static uint32_t enc(float x) { return __half_as_ushort(__float2half_rn(x * 32768.0f)); }
+    static constexpr int SL = 15;
+    __device__ static float dec_g(uint32_t c) { return __half2float(__ushort_as_half((unsigned short)c)); }
+    __device__ static uint32_t enc_g(float g) { return __half_as_ushort(__float2half_rn(g)); }
+    __device__ static float dec(uint32_t c) { return dec_g(c) * 3.0517578125e-5f; }
+    __device__ static uint32_t enc(float x) { return enc_g(x * 32768.0f); }
 };
 template <> struct Codec16<4> {   // FP16C (Sec. 3.1.4)
-    __device__ static float dec(uint32_t c) { return fp16c_decode(c); }
-    __device__ static uint32_t enc(float x) { return fp16c_encode(x); }
+    static constexpr int SL = 0;
+    __device__ static float dec_g(uint32_t c) { return fp16c_decode(c); }
+    __device__ static uint32_t enc_g(float g) { return fp16c_encode(g); }
+    __device__ static float dec(uint32_t c) { return dec_g(c); }
+    __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
+// The S posits encode |x| * 2^7 with the sign of x itself, so a NaN
+// saturates with its own sign whatever sign the hardware gives NaN * 128.
 template <> struct Codec16<5> {   // P16_0S: posit es=0 of x * 2^7
+    static constexpr int SL = 7;
+    __device__ static float dec_g(uint32_t c) { return posit_decode<0>(c, 0); }
+    __device__ static uint32_t enc_g(float g) { return p160_encode(fabsf(g)) | ((u32(g) >> 16) & 0x8000u); }
     __device__ static float dec(uint32_t c) { return posit_decode<0>(c, -7); }
-    __device__ static uint32_t enc(float x) { return p160_encode(x * 128.0f); }
+    __device__ static uint32_t enc(float x) {
+        return p160_encode(fabsf(x) * 128.0f) | ((u32(x) >> 16) & 0x8000u);
+    }
 };
 template <> struct Codec16<6> {   // P16_1S: posit es=1 of x * 2^7
+    static constexpr int SL = 7;
+    __device__ static float dec_g(uint32_t c) { return posit_decode<1>(c, 0); }
+    __device__ static uint32_t enc_g(float g) { return p161_encode(fabsf(g)) | ((u32(g) >> 16) & 0x8000u); }
     __device__ static float dec(uint32_t c) { return posit_decode<1>(c, -7); }
-    __device__ static uint32_t enc(float x) { return p161_encode(x * 128.0f); }
+    __device__ static uint32_t enc(float x) {
+        return p161_encode(fabsf(x) * 128.0f) | ((u32(x) >> 16) & 0x8000u);
+    }
 };
 template <> struct Codec16<7> {   // P16_2C
-    __device__ static float dec(uint32_t c) { return p162c_decode(c); }
-    __device__ static uint32_t enc(float x) { return p162c_encode(x); }
+    static constexpr int SL = 0;
+    __device__ static float dec_g(uint32_t c) { return p162c_decode(c); }
+    __device__ static uint32_t enc_g(float g) { return p162c_encode(g); }
+    __device__ static float dec(uint32_t c) { return dec_g(c); }
+    __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
 template <> struct Codec16<8> {   // P16_0, unscaled
-    __device__ static float dec(uint32_t c) { return posit_decode<0>(c, 0); }
-    __device__ static uint32_t enc(float x) { return p160_encode(x); }
+    static constexpr int SL = 0;
+    __device__ static float dec_g(uint32_t c) { return posit_decode<0>(c, 0); }
+    __device__ static uint32_t enc_g(float g) { return p160_encode(g); }
+    __device__ static float dec(uint32_t c) { return dec_g(c); }
+    __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
 template <> struct Codec16<9> {   // P16_1, unscaled
-    __device__ static float dec(uint32_t c) { return posit_decode<1>(c, 0); }
-    __device__ static uint32_t enc(float x) { return p161_encode(x); }
+    static constexpr int SL = 0;
+    __device__ static float dec_g(uint32_t c) { return posit_decode<1>(c, 0); }
+    __device__ static uint32_t enc_g(float g) { return p161_encode(g); }
+    __device__ static float dec(uint32_t c) { return dec_g(c); }
+    __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
 
-// Storage traits: FMT is the lbm.h storage id.
+// Storage traits: FMT is the lbm.h storage id.  load/store handle population
+// values; load_g/store_g handle values scaled by 2^SL (see Codec16).
 template <int FMT> struct Storage {
     using T = uint16_t;
     static constexpr int bytes = 2;
+    static constexpr int SL = Codec16<FMT>::SL;
+    template <class R> __device__ static R load_g(const T* p, size_t i) { return (R)Codec16<FMT>::dec_g(p[i]); }
+    template <class R> __device__ static void store_g(T* p, size_t i, R g) {
+        p[i] = (uint16_t)Codec16<FMT>::enc_g((float)g);
+    }
     template <class R> __device__ static R load(const T* p, size_t i) { return (R)Codec16<FMT>::dec(p[i]); }
     template <class R> __device__ static void store(T* p, size_t i, R v) {
         p[i] = (uint16_t)Codec16<FMT>::enc((float)v);
@@ -281,14 +318,20 @@ template <int FMT> struct Storage {
 template <> struct Storage<0> {   // FP64
     using T = double;
     static constexpr int bytes = 8;
+    static constexpr int SL = 0;
     template <class R> __device__ static R load(const T* p, size_t i) { return (R)p[i]; }
     template <class R> __device__ static void store(T* p, size_t i, R v) { p[i] = (double)v; }
+    template <class R> __device__ static R load_g(const T* p, size_t i) { return (R)p[i]; }
+    template <class R> __device__ static void store_g(T* p, size_t i, R v) { p[i] = (double)v; }
 };
 template <> struct Storage<1> {   // FP32
     using T = float;
     static constexpr int bytes = 4;
+    static constexpr int SL = 0;
     template <class R> __device__ static R load(const T* p, size_t i) { return (R)p[i]; }
     template <class R> __device__ static void store(T* p, size_t i, R v) { p[i] = (float)v; }
+    template <class R> __device__ static R load_g(const T* p, size_t i) { return (R)p[i]; }
+    template <class R> __device__ static void store_g(T* p, size_t i, R v) { p[i] = (float)v; }
 };
 
 // ---------------------------------------------------------------- collision
@@ -343,29 +386,50 @@ __device__ __forceinline__ R jsum(const R* f, R s) {
     }
 }
 
-// density (index order, +1 last: Sec. 2.2) and the alternating-sign momentum
-// sums over opposite pairs (Sec. 2.2, e.g. u_x = f1 - f2 + f7 - f8 + ...)
-template <class V, class R>
-__device__ __forceinline__ void moments(const R* f, R& rho, R* j) {
-    rho = f[0];
-    static_for<1, V::Q>([&](auto I) { rho = rho + f[I.value]; });
-    rho = rho + R(1);
-    j[0] = jsum<V, 0, 1, true, R>(f, R(0));
-    j[1] = jsum<V, 1, 1, true, R>(f, R(0));
-    j[2] = jsum<V, 2, 1, true, R>(f, R(0));
+// 2^SL and 2^-SL as exact constants
+template <int SL> struct Pow2 {
+    static constexpr double up = (double)(1ull << SL);
+    static constexpr double down = 1.0 / (double)(1ull << SL);
+};
+
+// Populations g = 2^SL f (SL = 0: unscaled).  Density in index order with 1
+// added last (Sec. 2.2): rho = (sum f) + 1, the exact sum of the scaled
+// values times 2^-SL being fused into that last addition; the momentum j is
+// returned scaled (alternating-sign sums over opposite pairs, Sec. 2.2).
+template <class V, class R, int SL>
+__device__ __forceinline__ void moments(const R* g, R& rho, R* j) {
+    R s = g[0];
+    static_for<1, V::Q>([&](auto I) { s = s + g[I.value]; });
+    if constexpr (SL == 0) rho = s + R(1);
+    else rho = fmaR(s, R(Pow2<SL>::down), R(1));
+    j[0] = jsum<V, 0, 1, true, R>(g, R(0));
+    j[1] = jsum<V, 1, 1, true, R>(g, R(0));
+    j[2] = jsum<V, 2, 1, true, R>(g, R(0));
 }
 
-// u = (j + F/2) / rho (Guo), before clamping
-template <class R>
+// u = (1/rho) (j + F/2) (appendix velocity equation, Guo half-force), before
+// clamping; j is the scaled momentum
+template <class R, int SL>
 __device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
+    const R inv = R(1) / rho;
+    if (k.force) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = (k.force ? fmaR(R(0.5), k.F[a], j[a]) : j[a]) / rho;
+        for (int a = 0; a < 3; ++a) {
+            const R jj = SL == 0 ? j[a] : j[a] * R(Pow2<SL>::down);
+            u[a] = fmaR(R(0.5), k.F[a], jj) * inv;
+        }
+    } else {
+        const R inv_g = SL == 0 ? inv : inv * R(Pow2<SL>::down);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = j[a] * inv_g;
+    }
 }
 
 // Shifted equilibrium with three FMAs per population (footnote of Sec. 2.2):
-// f^eq-s = A (0.5 (B^2 + C) +- B) + D, A = w rho, B = 3 u.c, C = -3 u.u, D = w (rho - 1).
-// Bp receives B of the first member of every pair.
-template <class V, class R>
+// f^eq-s = A (0.5 (B^2 + C) +- B) + D, A = w rho, B = 3 u.c, C = -3 u.u, D = w (rho - 1),
+// returned times 2^SL (the weights carry the scale).  Bp receives B of the
+// first member of every pair.
+template <class V, class R, int SL>
 __device__ __forceinline__ void equilibrium(R rho, const R* u, R* feq, R* Bp) {
     R t = u[0] * u[0];
     t = t + u[1] * u[1];
@@ -373,11 +437,11 @@ __device__ __forceinline__ void equilibrium(R rho, const R* u, R* feq, R* Bp) {
     const R C = R(-3) * t;
     const R u3[3] = {R(3) * u[0], R(3) * u[1], R(3) * u[2]};
     const R rhom1 = rho - R(1);
-    const R w0 = R(V::w(0));
+    const R w0 = R(V::w(0) * Pow2<SL>::up);
     feq[0] = fmaR(w0 * rho, R(0.5) * C, w0 * rhom1);
     static_for<0, (V::Q - 1) / 2>([&](auto K) {
         constexpr int p = 2 * K.value + 1;
-        const R w = R(V::w(p));
+        const R w = R(V::w(p) * Pow2<SL>::up);
         const R A = w * rho, D = w * rhom1;
         const R B = csum<V, p, R>(u3);
         const R X = fmaR(B, B, C);
@@ -387,33 +451,33 @@ __device__ __forceinline__ void equilibrium(R rho, const R* u, R* feq, R* Bp) {
     });
 }
 
-// Guo source S_i = 3 w_i ((c_i.F - u.F) + B_i (c_i.F)) with B_i = 3 c_i.u
-template <class V, class R>
+// Guo source S_i = 3 w_i ((c_i.F - u.F) + B_i (c_i.F)) with B_i = 3 c_i.u, times 2^SL
+template <class V, class R, int SL>
 __device__ __forceinline__ void guo_source(const Relax<R>& k, const R* u, const R* Bp, R* S) {
     R uF = u[0] * k.F[0];
     uF = fmaR(u[1], k.F[1], uF);
     if constexpr (V::D == 3) uF = fmaR(u[2], k.F[2], uF);
-    S[0] = R(3.0 * V::w(0)) * (-uF);
+    S[0] = R(3.0 * V::w(0) * Pow2<SL>::up) * (-uF);
     static_for<0, (V::Q - 1) / 2>([&](auto K) {
         constexpr int p = 2 * K.value + 1;
         const R cF = csum<V, p, R>(k.F);
-        const R w3 = R(3.0 * V::w(p));
+        const R w3 = R(3.0 * V::w(p) * Pow2<SL>::up);
         S[p] = w3 * fmaR(Bp[p], cF, cF - uF);
         S[p + 1] = w3 * fmaR(Bp[p], cF, (-cF) - uF);
     });
 }
 
-// streamed populations f -> post-collision populations (in place)
-template <class V, int COLL, class R>
+// streamed populations g -> post-collision populations (in place), both 2^SL f
+template <class V, int COLL, class R, int SL>
 __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
     R rho, j[3], u[3];
-    moments<V, R>(f, rho, j);
-    velocity<R>(k, rho, j, u);
+    moments<V, R, SL>(f, rho, j);
+    velocity<R, SL>(k, rho, j, u);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = minR(maxR(u[a], -k.cs), k.cs);
     R feq[V::Q], Bp[V::Q], S[V::Q];
-    equilibrium<V, R>(rho, u, feq, Bp);
-    if (k.force) guo_source<V, R>(k, u, Bp, S);
+    equilibrium<V, R, SL>(rho, u, feq, Bp);
+    if (k.force) guo_source<V, R, SL>(k, u, Bp, S);
     if constexpr (COLL == 0) {   // SRT: fma(1 - omega, f, omega f^eq)
         if (k.force) {
             static_for<0, V::Q>([&](auto I) {
@@ -445,10 +509,10 @@ __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
     }
 }
 
-template <class V, class R>
+template <class V, class R, int SL>
 __device__ __forceinline__ void equilibrium_only(R rho, const R* u, R* feq) {
     R Bp[V::Q];
-    equilibrium<V, R>(rho, u, feq, Bp);
+    equilibrium<V, R, SL>(rho, u, feq, Bp);
 }
 
 }  // namespace lbm

@@ -1,8 +1,8 @@
 // Ensembles: many independent lattices of uneven size advanced by ONE kernel
-// launch per time step.  The members' cells are cut into thread-block tiles
-// (bx x by cells of one xy-plane); a prefix-sum table maps a block index to
-// its member and tile, and a device table holds each member's pointers,
-// sizes and relaxation constants.  Steps are replayed from a CUDA graph of
+// launch per time step.  The members' cells are cut into tiles of `tile`
+// consecutive cells (one thread block each); a per-tile table names the
+// member, and a device table holds each member's pointers, sizes,
+// relaxation constants and division magic numbers.  Steps are replayed from a CUDA graph of
 // kGraphSteps launches.  Every cell runs the same per-cell routine as the
 // single-lattice kernel, so results are bit-for-bit those of one launch per
 // member.
@@ -26,9 +26,10 @@ struct lbm_ensemble {
     KernelSet* ks = nullptr;
     bool fp64 = false, aa = false;
     void* table = nullptr;          // EnsMember<R>[count]
-    int* tile_start = nullptr;      // count + 1
+    uint32_t* tile_member = nullptr;
+    size_t table_bytes = 0, tiles_alloc = 0;
     int total_tiles = 0;
-    int bx = 32, by = 8;
+    int tile = 256;                 // cells per tile = threads per block
     int64_t s = 0;                  // steps taken through the ensemble
     std::vector<int64_t> t0;        // member step counters at creation
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -47,11 +48,24 @@ struct lbm_ensemble {
 
 namespace {
 
+// floor(n / d) = umulhi(n, magic) >> shift for every n < 2^31 (d >= 2):
+// shift + 32 = 31 + ceil(log2 d), magic = ceil(2^(31 + ceil(log2 d)) / d)
+FastDiv make_div(uint32_t d) {
+    FastDiv f{0u, 0u, 0u};
+    if (d <= 1) { f.one = 1u; return f; }
+    uint32_t lg = 0;
+    while ((1ull << lg) < d) ++lg;
+    const unsigned long long num = 1ull << (31 + lg);
+    f.magic = (uint32_t)((num + d - 1) / d);
+    f.shift = lg - 1;
+    return f;
+}
+
 template <class R>
-std::vector<EnsMember<R>> make_table(lbm_ensemble* e, std::vector<int>& starts) {
+std::vector<EnsMember<R>> make_table(lbm_ensemble* e, std::vector<uint32_t>& tile_member) {
     std::vector<EnsMember<R>> tab(e->m.size());
-    starts.assign(e->m.size() + 1, 0);
-    long long total = 0;
+    tile_member.clear();
+    uint32_t total = 0;
     for (size_t k = 0; k < e->m.size(); ++k) {
         lbm_handle* h = e->m[k];
         const Relax<R>* rk_ptr;
@@ -60,32 +74,42 @@ std::vector<EnsMember<R>> make_table(lbm_ensemble* e, std::vector<int>& starts) 
         EnsMember<R>& M = tab[k];
         M.args[0] = h->args(rk, e->aa ? 0 : h->cur);
         M.args[1] = h->args(rk, e->aa ? 0 : 1 - h->cur);
-        M.tiles_x = (h->p.nx + e->bx - 1) / e->bx;
-        M.tiles_y = (h->p.ny + e->by - 1) / e->by;
-        starts[k] = (int)total;
-        total += (long long)M.tiles_x * M.tiles_y * h->p.nz;
+        M.ncells = (uint32_t)h->N;
+        M.tile0 = total;
+        M.by_plane = make_div((uint32_t)h->plane());
+        M.by_nx = make_div((uint32_t)h->p.nx);
+        const uint32_t tiles = (uint32_t)((h->N + e->tile - 1) / e->tile);
+        tile_member.insert(tile_member.end(), tiles, (uint32_t)k);
+        total += tiles;
     }
-    starts[e->m.size()] = (int)total;
     e->total_tiles = (int)total;
     return tab;
 }
 
 lbm_status upload_table(lbm_ensemble* e) {
-    std::vector<int> starts;
+    std::vector<uint32_t> tiles;
     size_t bytes;
     const void* src;
     std::vector<EnsMember<float>> tf;
     std::vector<EnsMember<double>> td;
-    if (e->fp64) { td = make_table<double>(e, starts); src = td.data(); bytes = td.size() * sizeof(EnsMember<double>); }
-    else { tf = make_table<float>(e, starts); src = tf.data(); bytes = tf.size() * sizeof(EnsMember<float>); }
+    if (e->fp64) { td = make_table<double>(e, tiles); src = td.data(); bytes = td.size() * sizeof(EnsMember<double>); }
+    else { tf = make_table<float>(e, tiles); src = tf.data(); bytes = tf.size() * sizeof(EnsMember<float>); }
+    if (e->cuda(cudaStreamSynchronize(e->stream), "sync")) return LBM_ERR_CUDA;
     if (!e->table) {
         if (e->cuda(cudaMalloc(&e->table, bytes), "table alloc")) return LBM_ERR_OOM;
-        if (e->cuda(cudaMalloc((void**)&e->tile_start, starts.size() * sizeof(int)), "table alloc")) return LBM_ERR_OOM;
+        e->table_bytes = bytes;
+    }
+    if (tiles.size() > e->tiles_alloc) {
+        if (e->tile_member) cudaFree(e->tile_member);
+        e->tile_member = nullptr;
+        if (e->cuda(cudaMalloc((void**)&e->tile_member, tiles.size() * sizeof(uint32_t)), "table alloc"))
+            return LBM_ERR_OOM;
+        e->tiles_alloc = tiles.size();
     }
     if (e->cuda(cudaMemcpyAsync(e->table, src, bytes, cudaMemcpyHostToDevice, e->stream), "table upload"))
         return LBM_ERR_CUDA;
-    if (e->cuda(cudaMemcpyAsync(e->tile_start, starts.data(), starts.size() * sizeof(int), cudaMemcpyHostToDevice,
-                                e->stream), "table upload"))
+    if (e->cuda(cudaMemcpyAsync(e->tile_member, tiles.data(), tiles.size() * sizeof(uint32_t),
+                                cudaMemcpyHostToDevice, e->stream), "table upload"))
         return LBM_ERR_CUDA;
     if (e->cuda(cudaStreamSynchronize(e->stream), "sync")) return LBM_ERR_CUDA;
     e->drop_graphs();
@@ -95,13 +119,13 @@ lbm_status upload_table(lbm_ensemble* e) {
 // kernel launch of ensemble step number `s` (0-based since creation)
 lbm_status launch(lbm_ensemble* e, int64_t s, cudaStream_t stream) {
     Launch L;
-    L.block = dim3(e->bx, e->by, 1);
+    L.block = dim3(e->tile, 1, 1);
     L.grid = dim3(e->total_tiles, 1, 1);
     L.stream = stream;
     const int64_t t = e->t0[0] + s;
     const int scheme = !e->aa ? SCHEME_AB : ((t & 1) ? SCHEME_AA_LOC : SCHEME_AA_PP);
     const int parity = e->aa ? 0 : (int)(s & 1);
-    return e->cuda(e->ks->ens[scheme](e->table, e->tile_start, (int)e->m.size(), parity, L), "ensemble kernel");
+    return e->cuda(e->ks->ens[scheme](e->table, e->tile_member, parity, L), "ensemble kernel");
 }
 
 lbm_status check_members(lbm_ensemble* e) {
@@ -168,7 +192,7 @@ extern "C" lbm_status lbm_ensemble_destroy(lbm_ensemble* e) {
     cudaStreamSynchronize(e->stream);
     e->drop_graphs();
     if (e->table) cudaFree(e->table);
-    if (e->tile_start) cudaFree(e->tile_start);
+    if (e->tile_member) cudaFree(e->tile_member);
     if (e->capture) cudaStreamDestroy(e->capture);
     delete e;
     return LBM_OK;
@@ -220,19 +244,18 @@ extern "C" lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps) {
 }
 
 extern "C" lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by) {
-    if (!e || bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32 != 0) return LBM_ERR_ARG;
+    if (!e || bx < 32 || by != 1 || bx > 256 || (bx % 32) != 0) return LBM_ERR_ARG;
     lbm_status st = check_members(e);
     if (st != LBM_OK) return st;
-    e->bx = bx;
-    e->by = by;
+    e->tile = bx;
     return upload_table(e);
 }
 
 extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx_out, int* by_out) {
     if (!e || trial_steps < 1) return LBM_ERR_ARG;
-    static const int shapes[][2] = {{32, 8}, {64, 4}, {128, 2}, {16, 16}, {32, 4}, {64, 2}, {16, 8}, {128, 1}};
+    static const int shapes[][2] = {{256, 1}, {128, 1}, {64, 1}, {192, 1}, {96, 1}};
     float best = INFINITY;
-    int bb[2] = {e->bx, e->by};
+    int bb[2] = {e->tile, 1};
     cudaEvent_t ev[2];
     if (e->cuda(cudaEventCreate(&ev[0]), "event") || e->cuda(cudaEventCreate(&ev[1]), "event")) return LBM_ERR_CUDA;
     lbm_status st = LBM_OK;

@@ -27,9 +27,9 @@ cudaError_t launch_step(const void* args, const Launch& L) {
 }
 
 template <class V, int COLL, int SCHEME>
-cudaError_t launch_ens(const void* members, const int* tile_start, int count, int parity, const Launch& L) {
+cudaError_t launch_ens(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
     k_ensemble_step<V, COLL, FMT, Real, SCHEME><<<L.grid, L.block, 0, L.stream>>>(
-        static_cast<const EnsMember<Real>*>(members), tile_start, count, parity);
+        static_cast<const EnsMember<Real>*>(members), tile_member, parity);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,10 @@ enum { SCHEME_AB = 0, SCHEME_AA_PP = 1, SCHEME_AA_LOC = 2 };
 enum { LAYOUT_AB = 0, LAYOUT_AA_SWAPPED = 1, LAYOUT_AA_NATURAL = 2 };
 enum { PROBE_FIELDS = 0, PROBE_F = 1, PROBE_REDUCE = 2 };
 
-// internal flag bit set by the library: a neighbour is a moving wall
+// internal flag bits of non-solid cells, set by the library after upload:
+// a neighbour is solid (or the cell is an outflow cell), a neighbour is a
+// moving wall
+constexpr uint32_t F_NEAR_SOLID = 0x20u;
 constexpr uint32_t F_NEAR_MOVING = 0x80u;
 
 template <class R> struct StepArgs {
@@ -63,71 +66,84 @@ struct Nbr {
 
 // Moving-wall term of the bounce-back (Sec. 4.4): 6 w_i rho_w (c_i . u_w),
 // rho_w = 1, u_w read at the wall cell m.
-template <class V, int I, class R>
+template <class V, int I, class R, int SL>
 __device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t m) {
     const R uw[3] = {(R)node_u[m], (R)node_u[N + m], (R)node_u[2 * N + m]};
-    return R(6.0 * V::w(I)) * csum<V, I, R>(uw);
+    return R(6.0 * V::w(I) * Pow2<SL>::up) * csum<V, I, R>(uw);
 }
 
-// Streamed population i of the cell that streams at `nb` (A-B or the first
-// A-A half).  A solid upstream cell reflects the cell's own opposite
-// population (mid-grid bounce-back), plus the moving-wall term; a free-slip
-// upstream cell (A-B only) hands over the mirror population of the cell next
-// to it, falling back to bounce-back if that cell is solid too.
-template <class V, int FMT, class R, bool FLAGS, bool AA, int I>
-__device__ __forceinline__ R pull(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
-                                  const Nbr& nb) {
+// Streamed populations of a cell next to solid cells (or an outflow cell),
+// streaming at `nb`.  A solid upstream cell reflects the cell's own opposite
+// population (mid-grid bounce-back, Sec. 4.1), plus the moving-wall term; a
+// free-slip upstream cell (A-B only) hands over the mirror population of the
+// cell beside it, or bounce-back if that cell is solid too.  Addresses are
+// chosen with selects and all loads are issued before the moving-wall terms
+// are added, so the loads stay in flight together.
+template <class V, int FMT, class R, bool AA>
+__device__ __forceinline__ void gather_boundary(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
+                                                const Nbr& nb, R* f) {
     using S = Storage<FMT>;
     const size_t N = a.N;
-    const uint32_t j = nb.up<V, I>();
-    constexpr int slot = AA ? opposite(I) : I;
-    if (!FLAGS) return S::template load<R>(src, (size_t)slot * N + j);
-    const uint32_t fy = a.flags[j];
-    if (!(fy & F_WALL)) return S::template load<R>(src, (size_t)slot * N + j);
-    if constexpr (!AA) {
-        if (fy & F_FREESLIP) {
-            const int axis = (fy >> 5) & 3;
-            if (axis < 3) {
-                constexpr int cx = V::c(I, 0), cy = V::c(I, 1), cz = V::c(I, 2);
-                constexpr int m0 = mirror<V>(I, 0), m1 = mirror<V>(I, 1), m2 = mirror<V>(I, 2);
-                const uint32_t j2 = nb.xo[axis == 0 ? 1 : 1 - cx] + nb.yo[axis == 1 ? 1 : 1 - cy] +
-                                    nb.zo[axis == 2 ? 1 : 1 - cz];
-                if (!(a.flags[j2] & F_WALL)) {
-                    const int mi = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
-                    return S::template load<R>(src, (size_t)mi * N + j2);
-                }
-            }
+    const uint32_t self = nb.self();
+    uint32_t fy[V::Q];
+    static_for<0, V::Q>([&](auto I) { fy[I.value] = a.flags[nb.up<V, I.value>()]; });
+    static_for<0, V::Q>([&](auto I) {
+        constexpr int i = I.value;
+        constexpr int slot = AA ? opposite(i) : i;
+        constexpr int bslot = AA ? i : opposite(i);
+        const uint32_t j = nb.up<V, i>();
+        const bool wall = fy[i] & F_WALL;
+        size_t addr = wall ? (size_t)bslot * N + self : (size_t)slot * N + j;
+        if constexpr (!AA) {
+            constexpr int cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
+            constexpr int m0 = mirror<V>(i, 0), m1 = mirror<V>(i, 1), m2 = mirror<V>(i, 2);
+            const uint32_t axis = (fy[i] >> 5) & 3u;
+            const bool fs = wall && (fy[i] & F_FREESLIP) && axis < 3u;
+            const uint32_t j2 = nb.xo[axis == 0 ? 1 : 1 - cx] + nb.yo[axis == 1 ? 1 : 1 - cy] +
+                                nb.zo[axis == 2 ? 1 : 1 - cz];
+            const uint32_t f2 = fs ? (uint32_t)a.flags[j2] : F_WALL;
+            if (!(f2 & F_WALL)) addr = (size_t)(axis == 0 ? m0 : (axis == 1 ? m1 : m2)) * N + j2;
         }
-    }
-    constexpr int bslot = AA ? I : opposite(I);
-    R v = S::template load<R>(src, (size_t)bslot * N + nb.self());
-    if (fy & F_MOVING) v = v + moving_term<V, I, R>(a.node_u, N, j);
-    return v;
+        f[i] = S::template load_g<R>(src, addr);
+    });
+    static_for<0, V::Q>([&](auto I) {
+        constexpr int i = I.value;
+        if (fy[i] & F_MOVING) f[i] = f[i] + moving_term<V, i, R, S::SL>(a.node_u, N, nb.up<V, i>());
+    });
 }
 
 // Streamed populations of cell n at (x,y,z) for the given memory layout.
+// Cells without solid neighbours (internal bit F_NEAR_SOLID clear) take the
+// plain pull, as in the flag-free kernel.
 template <class V, int FMT, class R, bool FLAGS, int LAYOUT>
 __device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
                                        int x, int y, int z, uint32_t n, uint32_t fl, R* f) {
     using S = Storage<FMT>;
     if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {
         static_for<0, V::Q>([&](auto I) {
-            f[I.value] = S::template load<R>(src, (size_t)I.value * a.N + n);
+            f[I.value] = S::template load_g<R>(src, (size_t)I.value * a.N + n);
         });
         if (FLAGS && (fl & F_NEAR_MOVING)) {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
             static_for<1, V::Q>([&](auto I) {
                 const uint32_t j = nb.up<V, I.value>();
-                if (a.flags[j] & F_MOVING) f[I.value] = f[I.value] + moving_term<V, I.value, R>(a.node_u, a.N, j);
+                if (a.flags[j] & F_MOVING) f[I.value] = f[I.value] + moving_term<V, I.value, R, S::SL>(a.node_u, a.N, j);
             });
         }
     } else {
-        int sx = x;
-        if (FLAGS && LAYOUT == LAYOUT_AB && (fl & F_OUTFLOW)) sx = x == 0 ? a.nx - 1 : x - 1;
-        const Nbr nb(sx, y, z, a.nx, a.ny, a.nz);
-        static_for<0, V::Q>([&](auto I) {
-            f[I.value] = pull<V, FMT, R, FLAGS, LAYOUT == LAYOUT_AA_SWAPPED, I.value>(a, src, nb);
-        });
+        constexpr bool AA = LAYOUT == LAYOUT_AA_SWAPPED;
+        if (FLAGS && (fl & F_NEAR_SOLID)) {
+            int sx = x;
+            if (!AA && (fl & F_OUTFLOW)) sx = x == 0 ? a.nx - 1 : x - 1;
+            const Nbr nb(sx, y, z, a.nx, a.ny, a.nz);
+            gather_boundary<V, FMT, R, AA>(a, src, nb, f);
+        } else {
+            const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
+            static_for<0, V::Q>([&](auto I) {
+                constexpr int slot = AA ? opposite(I.value) : I.value;
+                f[I.value] = S::template load_g<R>(src, (size_t)slot * a.N + nb.up<V, I.value>());
+            });
+        }
     }
 }
 
@@ -148,29 +164,33 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     R f[V::Q];
     if (FLAGS && (fl & F_EQ)) {
         const R u[3] = {(R)a.node_u[n], (R)a.node_u[N + n], (R)a.node_u[2 * N + n]};
-        equilibrium_only<V, R>((R)a.node_rho[n], u, f);
+        equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f);
     } else {
         constexpr int LAYOUT = SCHEME == SCHEME_AB ? LAYOUT_AB
                              : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
         gather<V, FMT, R, FLAGS, LAYOUT>(a, src, x, y, z, n, fl, f);
-        collide<V, COLL, R>(a.k, f);
+        collide<V, COLL, R, S::SL>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
-        static_for<0, V::Q>([&](auto I) { S::template store<R>(dst, (size_t)I.value * N + n, f[I.value]); });
+        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(dst, (size_t)I.value * N + n, f[I.value]); });
     } else if constexpr (SCHEME == SCHEME_AA_LOC) {
         static_for<0, V::Q>([&](auto I) {
-            S::template store<R>(dst, (size_t)opposite(I.value) * N + n, f[I.value]);
+            S::template store_g<R>(dst, (size_t)opposite(I.value) * N + n, f[I.value]);
         });
     } else {
         const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
-        static_for<0, V::Q>([&](auto I) {
-            constexpr int i = I.value;
-            const uint32_t d = nb.down<V, i>();
-            if (FLAGS && (a.flags[d] & F_WALL))   // reflected back into this cell
-                S::template store<R>(dst, (size_t)opposite(i) * N + n, f[i]);
-            else
-                S::template store<R>(dst, (size_t)i * N + d, f[i]);
-        });
+        if (FLAGS && (fl & F_NEAR_SOLID)) {
+            static_for<0, V::Q>([&](auto I) {
+                constexpr int i = I.value;
+                const uint32_t d = nb.down<V, i>();
+                const bool wall = a.flags[d] & F_WALL;   // reflected back into this cell
+                S::template store_g<R>(dst, wall ? (size_t)opposite(i) * N + n : (size_t)i * N + d, f[i]);
+            });
+        } else {
+            static_for<0, V::Q>([&](auto I) {
+                S::template store_g<R>(dst, (size_t)I.value * N + nb.down<V, I.value>(), f[I.value]);
+            });
+        }
     }
 }
 
@@ -183,37 +203,35 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<R> a) {
 }
 
 // ---------------------------------------------------------------- ensemble
-// Many independent lattices in one launch.  Each member's cells are cut into
-// tiles of bx*by cells in one xy-plane; tile_start[m] is the first global
-// tile of member m (prefix sum, tile_start[count] = total).  A block finds
-// its member by binary search and updates one tile.
+// Many independent lattices in one launch.  Each member's cells, in linear
+// order n = x + nx (y + ny z), are cut into tiles of blockDim.x consecutive
+// cells; tile_member[b] names the member of block b.  Coordinates come from n
+// by multiply-high division with per-member magic numbers (exact for n < 2^31).
+struct FastDiv {
+    uint32_t magic, shift, one;   // one != 0: divisor 1
+    __device__ __forceinline__ uint32_t div(uint32_t n) const {
+        return one ? n : (__umulhi(n, magic) >> shift);
+    }
+};
+
 template <class R> struct EnsMember {
     StepArgs<R> args[2];       // args[p]: arguments for a step of parity p
-    int tiles_x, tiles_y;
+    uint32_t ncells, tile0;    // cells, first global tile of this member
+    FastDiv by_plane, by_nx;
 };
 
 template <class V, int COLL, int FMT, class R, int SCHEME>
 __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __restrict__ members,
-                                                        const int* __restrict__ tile_start, int count,
-                                                        int parity) {
-    const int b = blockIdx.x;
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (__ldg(tile_start + mid) <= b) lo = mid; else hi = mid - 1;
-    }
-    const EnsMember<R>& M = members[lo];
-    const int t = b - __ldg(tile_start + lo);
-    const int txy = M.tiles_x * M.tiles_y;
-    const int z = t / txy;
-    const int r = t - z * txy;
-    const int ty = r / M.tiles_x;
-    const int tx = r - ty * M.tiles_x;
+                                                        const uint32_t* __restrict__ tile_member, int parity) {
+    const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
+    const uint32_t n = (blockIdx.x - M.tile0) * blockDim.x + threadIdx.x;
+    if (n >= M.ncells) return;
     const StepArgs<R> a = M.args[parity];
-    const int x = tx * blockDim.x + threadIdx.x;
-    const int y = ty * blockDim.y + threadIdx.y;
-    if (x >= a.nx || y >= a.ny) return;
-    cell_step<V, COLL, FMT, R, SCHEME, true>(a, x, y, z);
+    const uint32_t z = M.by_plane.div(n);
+    const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
+    const uint32_t y = M.by_nx.div(r);
+    const uint32_t x = r - y * (uint32_t)a.nx;
+    cell_step<V, COLL, FMT, R, SCHEME, true>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- probes
@@ -245,9 +263,11 @@ __global__ void __launch_bounds__(256) k_probe(const ProbeArgs<R> p, int mode) {
             if (a.flags) gather<V, FMT, R, true, LAYOUT>(a, (const typename Storage<FMT>::T*)a.src, x, y, z, n, fl, f);
             else gather<V, FMT, R, false, LAYOUT>(a, (const typename Storage<FMT>::T*)a.src, x, y, z, n, fl, f);
         }
+        constexpr int SL = Storage<FMT>::SL;
         if (mode == PROBE_F) {
             static_for<0, V::Q>([&](auto I) {
-                p.out[(size_t)I.value * count + t] = solid ? 0.0 : (double)f[I.value];
+                const R v = SL == 0 ? f[I.value] : f[I.value] * R(Pow2<SL>::down);
+                p.out[(size_t)I.value * count + t] = solid ? 0.0 : (double)v;
             });
             continue;
         }
@@ -258,8 +278,8 @@ __global__ void __launch_bounds__(256) k_probe(const ProbeArgs<R> p, int mode) {
             for (int d = 0; d < 3; ++d) u[d] = (double)a.node_u[(size_t)d * a.N + n];
         } else {
             R rr, j[3], uu[3];
-            moments<V, R>(f, rr, j);
-            velocity<R>(a.k, rr, j, uu);
+            moments<V, R, SL>(f, rr, j);
+            velocity<R, SL>(a.k, rr, j, uu);
             rho = (double)rr;
             for (int d = 0; d < 3; ++d) u[d] = (double)uu[d];
         }
@@ -329,7 +349,7 @@ __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
             const R rho = p.in[0] ? (R)p.in[0][t] : R(1);
             const R u[3] = {p.in[1] ? (R)p.in[1][t] : R(0), p.in[2] ? (R)p.in[2][t] : R(0),
                             (V::D == 3 && p.in[3]) ? (R)p.in[3][t] : R(0)};
-            equilibrium_only<V, R>(rho, u, f);
+            equilibrium_only<V, R, 0>(rho, u, f);
         }
         static_for<0, V::Q>([&](auto I) {
             constexpr int slot = AA ? opposite(I.value) : I.value;
@@ -338,10 +358,11 @@ __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
     }
 }
 
-// Marks cells next to a moving wall (internal bit F_NEAR_MOVING), so the
-// in-place scheme adds the moving-wall term where it reads a reflected population.
+// Sets the internal bits of non-solid cells: F_NEAR_SOLID if any neighbour
+// is solid or the cell is an outflow cell, F_NEAR_MOVING if any neighbour is a
+// moving wall.
 template <class V>
-__global__ void k_mark_near_moving(uint8_t* flags, int nx, int ny, int nz) {
+__global__ void k_mark_neighbours(uint8_t* flags, int nx, int ny, int nz) {
     const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
     const uint32_t N = plane * (uint32_t)nz;
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
@@ -352,9 +373,12 @@ __global__ void k_mark_near_moving(uint8_t* flags, int nx, int ny, int nz) {
         const int y = (int)(r / (uint32_t)nx);
         const int x = (int)(r - (uint32_t)y * nx);
         const Nbr nb(x, y, z, nx, ny, nz);
-        bool near = false;
-        static_for<1, V::Q>([&](auto I) { near = near || (flags[nb.up<V, I.value>()] & F_MOVING); });
-        if (near) flags[n] = (uint8_t)(fl | F_NEAR_MOVING);
+        uint32_t any = 0;
+        static_for<1, V::Q>([&](auto I) { any |= flags[nb.up<V, I.value>()]; });
+        uint32_t add = 0;
+        if ((any & F_WALL) || (fl & F_OUTFLOW)) add |= F_NEAR_SOLID;
+        if (any & F_MOVING) add |= F_NEAR_MOVING;
+        if (add) flags[n] = (uint8_t)(fl | add);
     }
 }
 

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 namespace lbm {
 
@@ -12,8 +13,7 @@ struct Launch {
 };
 
 using StepFn = cudaError_t (*)(const void* step_args, const Launch&);
-using EnsFn = cudaError_t (*)(const void* members, const int* tile_start, int count, int parity,
-                              const Launch&);
+using EnsFn = cudaError_t (*)(const void* members, const uint32_t* tile_member, int parity, const Launch&);
 using ProbeFn = cudaError_t (*)(const void* probe_args, int mode, const Launch&);
 using PutFn = cudaError_t (*)(const void* put_args, int setf, const Launch&);
 

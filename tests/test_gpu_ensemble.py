@@ -41,7 +41,7 @@ def test_ensemble_equals_per_member_launches(scheme):
     eb.step_each(150)
     for ga, gb in zip(a, b):
         assert np.array_equal(ga.f(), gb.f())
-    ea.set_block(64, 4)
+    ea.set_block(64, 1)
     ea.step(3)
     eb.step_each(3)
     for ga, gb in zip(a, b):
