@@ -275,6 +275,7 @@ def main():
     fields = tg_fields(n)
     head_arith = "FP64" if args.format == "FP64" else "FP32"
     g = make_lattice(P, n, head_arith, args.format, args.scheme, fields)
+    variant_used = g.variant()
     g.step(args.warmup)
     m0, _ = g.reduce()
     if dist:
@@ -299,7 +300,7 @@ def main():
     tier_name = f"{head_arith}/{args.format}"
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": profiled_traffic(tier_name), "peak_kind": peak_kind,
-                "bytes_per_cell": bpc, "kernel": "k_step<D3Q19,SRT,%s,A-B,flag-free>" % args.format}
+                "bytes_per_cell": bpc, "kernel": "stream-collide D3Q19 SRT %s A-B flag-free, variant %s" % (args.format, variant_used)}
 
     # end to end through the C ABI with pinned host buffers
     pin = [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).reshape(-1)).pin_memory() for a in fields]
@@ -335,6 +336,19 @@ def main():
                                     "frac_hbm": b * N * steps / dt / 1e9 / peak, "bytes_per_cell": b,
                                     "roofline_mlups": peak * 1e3 / b, "steps": steps}
                 gg.close()
+            variants = {}
+            for v in ("generic", "paired", "staged"):
+                gg = make_lattice(P, n, head_arith, args.format, "AB", fields)
+                gg.set_variant(v)
+                if gg.variant() != v:
+                    gg.close()
+                    continue
+                gg.step(args.warmup)
+                steps = max(args.steps // 2, 10)
+                dt = time_steps(torch, gg, steps)
+                variants[v] = {"mlups": N * steps / dt / 1e6, "frac_hbm": bpc * N * steps / dt / 1e9 / peak}
+                gg.close()
+            per_format[f"{tier_name} kernel variants"] = variants
             gg = make_lattice(P, n, head_arith, args.format, "AA", fields)
             gg.step(args.warmup)
             steps = max(args.steps // 2, 10)

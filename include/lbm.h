@@ -42,7 +42,7 @@ typedef enum {
     LBM_ERR_CUDA = 3,         /* a CUDA runtime call failed */
     LBM_ERR_UNSUPPORTED = 4,  /* valid but unsupported combination */
     LBM_ERR_DIVERGED = 5,     /* FP64 mass check found a non-finite value */
-    LBM_ERR_TIMEOUT = 6,      /* reserved */
+    LBM_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out */
     LBM_ERR_STATE = 7         /* handle poisoned by an earlier CUDA error */
 } lbm_status;
 
@@ -110,8 +110,9 @@ lbm_status lbm_destroy(lbm_handle* h);
  * kernel of the paper's periodic benchmark box, Sec. 5); node_u: 3*N floats
  * component-major (ux[N], uy[N], uz[N]; wall velocity of MOVING cells, state
  * of EQ cells) or NULL (zero); node_rho: N floats (EQ density) or NULL (1).
- * With A-A streaming, OUTFLOW and FREESLIP cells give LBM_ERR_UNSUPPORTED.
- * Invalid bit combinations give LBM_ERR_ARG. */
+ * The populations of cells that are solid in the new geometry are set to
+ * zero.  With A-A streaming, OUTFLOW and FREESLIP cells give
+ * LBM_ERR_UNSUPPORTED.  Invalid bit combinations give LBM_ERR_ARG. */
 lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* node_u,
                             const float* node_rho);
 
@@ -147,6 +148,13 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f);
  * sum is not finite.  Synchronises the stream. */
 lbm_status lbm_reduce(lbm_handle* h, double* mass, double* kinetic_energy);
 
+/* memory layout of the populations: structure of arrays f[i*N + n], or the
+ * chunked layout of flag-free A-B lattices with 16-bit storage and nx a
+ * multiple of 64 (chosen by LBM_VARIANT_AUTO / _PAIRED): the cells of each
+ * row are cut into chunks of 64, and chunk c = n/64 holds its q populations
+ * one after the other, element ((n/64)*q + i)*64 + n%64. */
+enum { LBM_LAYOUT_SOA = 0, LBM_LAYOUT_CHUNKED = 1 };
+
 typedef struct {
     int q;                    /* populations per cell */
     int64_t cells;            /* N */
@@ -155,6 +163,7 @@ typedef struct {
     int has_flags;            /* 0: flag-free periodic kernel */
     size_t device_bytes;      /* bytes held on the device */
     void* ddf[2];             /* device population copies (ddf[1] NULL for A-A) */
+    int layout;               /* LBM_LAYOUT_SOA or LBM_LAYOUT_CHUNKED */
 } lbm_info;
 
 lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info);
@@ -162,6 +171,29 @@ lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info);
 /* Thread-block shape of the stream-collide launches (threads along x and y;
  * bx*by a multiple of 32, at most 1024).  Default 128 x 2. */
 lbm_status lbm_set_block(lbm_handle* h, int bx, int by);
+
+/* Stream-collide kernel variants; all give bit-for-bit the same result.
+ *   GENERIC  one cell per thread, every lattice and boundary kind;
+ *   PAIRED   two x-neighbouring cells per thread, populations moved as
+ *            32-bit pairs of codes (flag-free A-B lattices with 16-bit
+ *            storage, FP32 arithmetic, even nx, q*N < 2^32, block width a
+ *            multiple of 32); with nx a multiple of 64 it runs on the
+ *            chunked layout (LBM_LAYOUT_CHUNKED), every warp moving whole
+ *            128-byte lines at compile-time offsets;
+ *   STAGED   source rows prefetched into shared memory by bulk copies
+ *            several tiles ahead (flag-free A-B D3Q19 lattices, FP32
+ *            arithmetic, nx of 128, 256 or 512); a copy wait that runs out
+ *            (about a second) makes the next synchronising call return
+ *            LBM_ERR_TIMEOUT;
+ *   AUTO     (default) PAIRED where it applies, else GENERIC.
+ * A requested variant that does not apply falls back to GENERIC.  Switching
+ * variant, or setting flags, converts the stored populations between the
+ * layouts (no change in values). */
+enum { LBM_VARIANT_AUTO = 0, LBM_VARIANT_GENERIC = 1, LBM_VARIANT_STAGED = 2, LBM_VARIANT_PAIRED = 3 };
+lbm_status lbm_set_variant(lbm_handle* h, int variant);
+/* The variant lbm_step launches for h now (LBM_VARIANT_GENERIC, _STAGED or
+ * _PAIRED), or -1 for a NULL handle. */
+int lbm_get_variant(const lbm_handle* h);
 
 /* Same search as lbm_ensemble_autotune for one lattice; the trial steps
  * advance the lattice. */

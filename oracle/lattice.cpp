@@ -520,6 +520,10 @@ void orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u,
     if (L->vs.d == 2) std::fill(L->nu.begin() + 2 * N, L->nu.end(), 0.0f);
     if (node_rho) std::memcpy(L->nrho.data(), node_rho, N * sizeof(float));
     else std::fill(L->nrho.begin(), L->nrho.end(), 1.0f);
+    /* solid cells hold no populations */
+    for (int64_t n = 0; n < N; ++n)
+        if (L->solid(n))
+            for (int i = 0; i < L->vs.q; ++i) L->fa[i * N + n] = L->fb[i * N + n] = 0.0;
 }
 
 void orc_set_rho_u(orc_lattice* L, const double* rho, const double* ux, const double* uy, const double* uz) {

@@ -85,7 +85,8 @@ void orc_velset_table(int velset, int* c /* q*3 */, double* w /* q */);
 orc_lattice* orc_create(const orc_params* p);   /* NULL on bad parameters */
 void orc_destroy(orc_lattice* L);
 /* flags (N bytes), node_u (3*N floats, component-major: ux[N], uy[N], uz[N]) and
- * node_rho (N floats) may be NULL (all fluid / zero velocity / unit density) */
+ * node_rho (N floats) may be NULL (all fluid / zero velocity / unit density);
+ * the populations of solid cells are set to zero */
 void orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u,
                       const float* node_rho);
 /* initialise every non-solid cell with the shifted equilibrium of (rho, u) */

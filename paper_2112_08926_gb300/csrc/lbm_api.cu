@@ -57,6 +57,10 @@ template <class R> void make_relax(const lbm_params& p, Relax<R>& k) {
     k.force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;
 }
 
+bool want_chunked(const lbm_handle* h);
+lbm_status ensure_layout(lbm_handle* h);
+lbm_status zero_solid(lbm_handle* h);
+
 lbm_status check_handle(lbm_handle* h) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky != LBM_OK) return LBM_ERR_STATE;
@@ -78,6 +82,18 @@ struct Staging {
     }
     bool ok() const { return h->scratch != nullptr; }
 };
+
+// reads the device status word (call after a stream synchronisation)
+lbm_status check_status(lbm_handle* h) {
+    int st = 0;
+    if (h->cuda(cudaMemcpy(&st, h->status, sizeof(int), cudaMemcpyDeviceToHost), "status read")) return LBM_ERR_CUDA;
+    if (st) {
+        h->sticky = LBM_ERR_TIMEOUT;
+        h->err = "a kernel gave up waiting for its staged copies";
+        return LBM_ERR_TIMEOUT;
+    }
+    return LBM_OK;
+}
 
 }  // namespace
 
@@ -144,8 +160,19 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
     }
     h->scratch_doubles = std::max(kScratchDoubles, (size_t)h->plane() * std::max(h->q, 4));
     h->scratch_doubles = std::min(h->scratch_doubles, (size_t)std::max(h->q, 4) * N);
-    h->partial = (double*)h->alloc((2 * kReduceBlocks + 2) * sizeof(double));
+    h->partial = (double*)h->alloc((2 * kReduceBlocks + 2) * sizeof(double) + 256);
     if (!h->partial) { lbm_destroy(h); return LBM_ERR_OOM; }
+    h->status = (int*)(h->partial + 2 * kReduceBlocks + 2);
+    if (h->cuda(cudaMemsetAsync(h->status, 0, sizeof(int), h->stream), "memset")) {
+        lbm_destroy(h);
+        return LBM_ERR_CUDA;
+    }
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->num_sms <= 0) h->num_sms = 1;
+    }
     for (int c = 0; c < copies; ++c)
         if (h->cuda(cudaMemsetAsync(h->f[c], 0, fbytes, h->stream), "memset") != LBM_OK) {
             lbm_destroy(h);
@@ -180,7 +207,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         h->release((void*&)h->flags, N);
         h->release((void*&)h->node_u, 3 * N * sizeof(float));
         h->release((void*&)h->node_rho, N * sizeof(float));
-        return LBM_OK;
+        return ensure_layout(h);
     }
     bool any_moving = false, any_eq = false;
     for (size_t n = 0; n < N; ++n) {
@@ -243,6 +270,10 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         else k_mark_neighbours<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
         if (h->cuda(cudaGetLastError(), "mark kernel")) return LBM_ERR_CUDA;
     }
+    lbm_status st2 = ensure_layout(h);   // flags force the SoA layout
+    if (st2 != LBM_OK) return st2;
+    st2 = zero_solid(h);                 // solid cells hold no populations
+    if (st2 != LBM_OK) return st2;
     if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
     return LBM_OK;
 }
@@ -256,6 +287,7 @@ lbm_status put_all(lbm_handle* h, const Relax<R>& k, int setf, int per_cell, Up 
     const size_t fbytes = (size_t)h->q * h->N * h->sb;
     for (int c = 0; c < (h->aa() ? 1 : 2); ++c)
         if (h->cuda(cudaMemsetAsync(h->f[c], 0, fbytes, h->stream), "memset")) return LBM_ERR_CUDA;
+    h->chunked = want_chunked(h) ? 1 : 0;   // the populations are rewritten: take the best layout
     const int chunk = h->planes_per_chunk(per_cell);
     for (int z0 = 0; z0 < h->p.nz; z0 += chunk) {
         const int z1 = std::min(h->p.nz, z0 + chunk);
@@ -271,7 +303,7 @@ lbm_status put_all(lbm_handle* h, const Relax<R>& k, int setf, int per_cell, Up 
         L.block = dim3(256);
         L.grid = dim3((unsigned)std::min<size_t>((count + 255) / 256, 152 * 32));
         L.stream = h->stream;
-        if (h->cuda(h->ks->put[h->aa() ? 1 : 0](&pa, setf, L), "put kernel")) return LBM_ERR_CUDA;
+        if (h->cuda(h->ks->put[h->aa() ? 1 : (h->chunked ? 2 : 0)](&pa, setf, L), "put kernel")) return LBM_ERR_CUDA;
         if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
     }
     h->t = 0;
@@ -322,10 +354,117 @@ extern "C" lbm_status lbm_set_f(lbm_handle* h, const double* f) {
 
 namespace {
 
+// index of the staged kernel that applies to h, or -1
+int staged_index(const lbm_handle* h) {
+    if (h->flags || h->aa() || h->fp64() || h->p.velset != LBM_D3Q19 || !h->idx32()) return -1;
+    const int idx = h->p.nx == 128 ? 0 : (h->p.nx == 256 ? 1 : (h->p.nx == 512 ? 2 : -1));
+    if (idx < 0 || !h->ks->staged[idx]) return -1;
+    return idx;
+}
+
+// the chunked layout: flag-free A-B lattice, 16-bit storage, nx a multiple of 64
+bool chunk_eligible(const lbm_handle* h) {
+    return !h->flags && !h->aa() && !h->fp64() && h->sb == 2 && (h->p.nx % lbm::CHUNK) == 0 && h->idx32() &&
+           h->ks->pair_chunked;
+}
+bool want_chunked(const lbm_handle* h) {
+    return chunk_eligible(h) && (h->variant == LBM_VARIANT_AUTO || h->variant == LBM_VARIANT_PAIRED);
+}
+
+bool pair_applies(const lbm_handle* h) {
+    return !h->flags && !h->aa() && !h->fp64() && h->sb == 2 && (h->p.nx % 2) == 0 && h->idx32() &&
+           (h->bx % 32) == 0 && h->ks->pair;
+}
+
+// kernel variant lbm_step launches for h
+int variant_in_use(const lbm_handle* h) {
+    if (h->chunked) return LBM_VARIANT_PAIRED;
+    if (h->variant == LBM_VARIANT_STAGED && staged_index(h) >= 0) return LBM_VARIANT_STAGED;
+    // without the chunked layout the paired kernel pays off only with hardware
+    // conversions (FP16, FP16S); AUTO keeps the software codecs on GENERIC
+    const bool hw = h->p.storage == LBM_FP16 || h->p.storage == LBM_FP16S;
+    if ((h->variant == LBM_VARIANT_PAIRED || (h->variant == LBM_VARIANT_AUTO && hw)) && pair_applies(h))
+        return LBM_VARIANT_PAIRED;
+    return LBM_VARIANT_GENERIC;
+}
+
+// copies the population codes between the SoA and the chunked layout
+template <class V>
+__global__ void k_relayout(const uint16_t* __restrict__ src, uint16_t* __restrict__ dst, uint32_t N,
+                           int to_chunked) {
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int i = 0; i < V::Q; ++i) {
+            const uint32_t soa = (uint32_t)i * N + n, ch = lbm::chunk_elem<V>(i, n);
+            if (to_chunked) dst[ch] = src[soa];
+            else dst[soa] = src[ch];
+        }
+    }
+}
+
+// zeroes the populations of solid cells (SoA layout)
+template <class T>
+__global__ void k_zero_solid(const uint8_t* __restrict__ flags, T* f, int q, uint32_t N) {
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+        if (flags[n] & lbm::F_WALL)
+            for (int i = 0; i < q; ++i) f[(size_t)i * N + n] = T(0);
+}
+
+lbm_status zero_solid(lbm_handle* h) {
+    const unsigned grid = (unsigned)std::min<size_t>((h->N + 255) / 256, 152 * 32);
+    for (int c = 0; c < (h->aa() ? 1 : 2); ++c) {
+        if (h->sb == 8) k_zero_solid<double><<<grid, 256, 0, h->stream>>>(h->flags, (double*)h->f[c], h->q, (uint32_t)h->N);
+        else if (h->sb == 4) k_zero_solid<float><<<grid, 256, 0, h->stream>>>(h->flags, (float*)h->f[c], h->q, (uint32_t)h->N);
+        else k_zero_solid<uint16_t><<<grid, 256, 0, h->stream>>>(h->flags, (uint16_t*)h->f[c], h->q, (uint32_t)h->N);
+        if (h->cuda(cudaGetLastError(), "zero kernel")) return LBM_ERR_CUDA;
+    }
+    return LBM_OK;
+}
+
+// brings the stored populations into the layout the current settings call for
+lbm_status ensure_layout(lbm_handle* h) {
+    const int want = want_chunked(h) ? 1 : 0;
+    if (want == h->chunked) return LBM_OK;
+    if (h->aa()) { h->chunked = 0; return LBM_OK; }
+    const uint16_t* src = (const uint16_t*)h->f[h->cur];
+    uint16_t* dst = (uint16_t*)h->f[1 - h->cur];
+    const unsigned grid = (unsigned)std::min<size_t>((h->N + 255) / 256, 152 * 32);
+    if (h->p.velset == LBM_D2Q9) k_relayout<D2Q9><<<grid, 256, 0, h->stream>>>(src, dst, (uint32_t)h->N, want);
+    else if (h->p.velset == LBM_D3Q19) k_relayout<D3Q19><<<grid, 256, 0, h->stream>>>(src, dst, (uint32_t)h->N, want);
+    else k_relayout<D3Q27><<<grid, 256, 0, h->stream>>>(src, dst, (uint32_t)h->N, want);
+    if (h->cuda(cudaGetLastError(), "relayout kernel")) return LBM_ERR_CUDA;
+    h->cur = 1 - h->cur;
+    h->chunked = want;
+    return LBM_OK;
+}
+
 template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, cudaStream_t s) {
     const int scheme = h->scheme_now();
     const StepArgs<R> a = h->args(k, h->aa() ? 0 : h->cur);
-    const lbm_status st = h->cuda(h->ks->step[scheme][h->flags ? 1 : 0](&a, h->step_launch(s)), "step kernel");
+    const int variant = variant_in_use(h);
+    lbm_status st;
+    if (h->chunked) {
+        Launch L;
+        L.block = dim3(32, 8, 1);
+        L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
+        L.stream = s;
+        st = h->cuda(h->ks->pair_chunked(&a, L), "chunked step kernel");
+    } else if (variant == LBM_VARIANT_PAIRED) {
+        Launch L;
+        L.block = dim3(h->bx, h->by, 1);
+        L.grid = dim3((h->p.nx / 2 + h->bx - 1) / h->bx, (h->p.ny + h->by - 1) / h->by, h->p.nz);
+        L.stream = s;
+        st = h->cuda(h->ks->pair(&a, L), "paired step kernel");
+    } else if (variant == LBM_VARIANT_STAGED) {
+        const int si = staged_index(h);
+        const int rows = h->ks->staged_rows[si];
+        const int tiles_y = (h->p.ny + rows - 1) / rows;
+        const int grid = std::min(tiles_y * h->p.nz, 2 * h->num_sms);
+        st = h->cuda(h->ks->staged[si](&a, grid, tiles_y, h->status, s), "staged step kernel");
+    } else {
+        st = h->cuda(h->ks->step[scheme][h->flags ? 1 : 0][h->idx32() ? 1 : 0](&a, h->step_launch(s)),
+                     "step kernel");
+    }
     if (st != LBM_OK) return st;
     if (!h->aa()) h->cur ^= 1;
     h->t += 1;
@@ -391,8 +530,9 @@ extern "C" lbm_status lbm_get_rho_u(lbm_handle* h, double* rho, double* ux, doub
                 return LBM_ERR_CUDA;
         return h->cuda(cudaStreamSynchronize(h->stream), "sync");
     };
-    return h->fp64() ? probe_chunks(h, h->kd, PROBE_FIELDS, 4, download)
-                     : probe_chunks(h, h->kf, PROBE_FIELDS, 4, download);
+    st = h->fp64() ? probe_chunks(h, h->kd, PROBE_FIELDS, 4, download)
+                   : probe_chunks(h, h->kf, PROBE_FIELDS, 4, download);
+    return st == LBM_OK ? check_status(h) : st;
 }
 
 extern "C" lbm_status lbm_get_f(lbm_handle* h, double* f) {
@@ -409,8 +549,9 @@ extern "C" lbm_status lbm_get_f(lbm_handle* h, double* f) {
                 return LBM_ERR_CUDA;
         return h->cuda(cudaStreamSynchronize(h->stream), "sync");
     };
-    return h->fp64() ? probe_chunks(h, h->kd, PROBE_F, h->q, download)
-                     : probe_chunks(h, h->kf, PROBE_F, h->q, download);
+    st = h->fp64() ? probe_chunks(h, h->kd, PROBE_F, h->q, download)
+                   : probe_chunks(h, h->kf, PROBE_F, h->q, download);
+    return st == LBM_OK ? check_status(h) : st;
 }
 
 namespace {
@@ -448,6 +589,7 @@ template <class R> lbm_status reduce_impl(lbm_handle* h, const Relax<R>& k, doub
     double res[2];
     if (h->cuda(cudaMemcpyAsync(res, out, sizeof res, cudaMemcpyDeviceToHost, h->stream), "download")) return LBM_ERR_CUDA;
     if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
+    if (check_status(h) != LBM_OK) return LBM_ERR_TIMEOUT;
     if (mass) *mass = res[0];
     if (energy) *energy = res[1];
     if (!std::isfinite(res[0]) || !std::isfinite(res[1])) return h->fail(LBM_ERR_DIVERGED, "non-finite mass or energy");
@@ -472,6 +614,7 @@ extern "C" lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info) {
     info->device_bytes = h->device_bytes;
     info->ddf[0] = h->aa() ? h->f[0] : h->f[h->cur];
     info->ddf[1] = h->aa() ? nullptr : h->f[1 - h->cur];
+    info->layout = h->chunked ? LBM_LAYOUT_CHUNKED : LBM_LAYOUT_SOA;
     return LBM_OK;
 }
 
@@ -505,3 +648,12 @@ extern "C" lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx_out, 
     if (by_out) *by_out = bb[1];
     return st;
 }
+
+extern "C" lbm_status lbm_set_variant(lbm_handle* h, int variant) {
+    if (!h) return LBM_ERR_ARG;
+    if (variant < LBM_VARIANT_AUTO || variant > LBM_VARIANT_PAIRED) return h->fail(LBM_ERR_ARG, "variant");
+    h->variant = variant;
+    return ensure_layout(h);
+}
+
+extern "C" int lbm_get_variant(const lbm_handle* h) { return h ? variant_in_use(h) : -1; }

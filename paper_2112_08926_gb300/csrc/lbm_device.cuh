@@ -306,12 +306,12 @@ template <int FMT> struct Storage {
     using T = uint16_t;
     static constexpr int bytes = 2;
     static constexpr int SL = Codec16<FMT>::SL;
-    template <class R> __device__ static R load_g(const T* p, size_t i) { return (R)Codec16<FMT>::dec_g(p[i]); }
-    template <class R> __device__ static void store_g(T* p, size_t i, R g) {
+    template <class R, class IX> __device__ static R load_g(const T* p, IX i) { return (R)Codec16<FMT>::dec_g(p[i]); }
+    template <class R, class IX> __device__ static void store_g(T* p, IX i, R g) {
         p[i] = (uint16_t)Codec16<FMT>::enc_g((float)g);
     }
-    template <class R> __device__ static R load(const T* p, size_t i) { return (R)Codec16<FMT>::dec(p[i]); }
-    template <class R> __device__ static void store(T* p, size_t i, R v) {
+    template <class R, class IX> __device__ static R load(const T* p, IX i) { return (R)Codec16<FMT>::dec(p[i]); }
+    template <class R, class IX> __device__ static void store(T* p, IX i, R v) {
         p[i] = (uint16_t)Codec16<FMT>::enc((float)v);
     }
 };
@@ -319,19 +319,19 @@ template <> struct Storage<0> {   // FP64
     using T = double;
     static constexpr int bytes = 8;
     static constexpr int SL = 0;
-    template <class R> __device__ static R load(const T* p, size_t i) { return (R)p[i]; }
-    template <class R> __device__ static void store(T* p, size_t i, R v) { p[i] = (double)v; }
-    template <class R> __device__ static R load_g(const T* p, size_t i) { return (R)p[i]; }
-    template <class R> __device__ static void store_g(T* p, size_t i, R v) { p[i] = (double)v; }
+    template <class R, class IX> __device__ static R load(const T* p, IX i) { return (R)p[i]; }
+    template <class R, class IX> __device__ static void store(T* p, IX i, R v) { p[i] = (double)v; }
+    template <class R, class IX> __device__ static R load_g(const T* p, IX i) { return (R)p[i]; }
+    template <class R, class IX> __device__ static void store_g(T* p, IX i, R v) { p[i] = (double)v; }
 };
 template <> struct Storage<1> {   // FP32
     using T = float;
     static constexpr int bytes = 4;
     static constexpr int SL = 0;
-    template <class R> __device__ static R load(const T* p, size_t i) { return (R)p[i]; }
-    template <class R> __device__ static void store(T* p, size_t i, R v) { p[i] = (float)v; }
-    template <class R> __device__ static R load_g(const T* p, size_t i) { return (R)p[i]; }
-    template <class R> __device__ static void store_g(T* p, size_t i, R v) { p[i] = (float)v; }
+    template <class R, class IX> __device__ static R load(const T* p, IX i) { return (R)p[i]; }
+    template <class R, class IX> __device__ static void store(T* p, IX i, R v) { p[i] = (float)v; }
+    template <class R, class IX> __device__ static R load_g(const T* p, IX i) { return (R)p[i]; }
+    template <class R, class IX> __device__ static void store_g(T* p, IX i, R v) { p[i] = (float)v; }
 };
 
 // ---------------------------------------------------------------- collision

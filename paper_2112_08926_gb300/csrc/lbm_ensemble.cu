@@ -30,6 +30,7 @@ struct lbm_ensemble {
     size_t table_bytes = 0, tiles_alloc = 0;
     int total_tiles = 0;
     int tile = 256;                 // cells per tile = threads per block
+    bool idx32 = true;              // every member's q*N < 2^32
     int64_t s = 0;                  // steps taken through the ensemble
     std::vector<int64_t> t0;        // member step counters at creation
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
@@ -125,7 +126,7 @@ lbm_status launch(lbm_ensemble* e, int64_t s, cudaStream_t stream) {
     const int64_t t = e->t0[0] + s;
     const int scheme = !e->aa ? SCHEME_AB : ((t & 1) ? SCHEME_AA_LOC : SCHEME_AA_PP);
     const int parity = e->aa ? 0 : (int)(s & 1);
-    return e->cuda(e->ks->ens[scheme](e->table, e->tile_member, parity, L), "ensemble kernel");
+    return e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L), "ensemble kernel");
 }
 
 lbm_status check_members(lbm_ensemble* e) {
@@ -173,7 +174,10 @@ extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count,
     e->ks = h0->ks;
     e->fp64 = h0->fp64();
     e->aa = h0->aa();
-    for (lbm_handle* h : e->m) e->t0.push_back(h->t);
+    for (lbm_handle* h : e->m) {
+        e->t0.push_back(h->t);
+        e->idx32 = e->idx32 && h->idx32();
+    }
     if (cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking) != cudaSuccess) {
         delete e;
         return LBM_ERR_CUDA;

@@ -33,6 +33,10 @@ struct lbm_handle {
     int64_t t = 0;
     int cur = 0;
     int bx = 128, by = 2;
+    int variant = 0;           // requested stream-collide kernel variant (LBM_VARIANT_*)
+    int chunked = 0;           // populations in the chunked layout (flag-free A-B, 16-bit)
+    int num_sms = 0;
+    int* status = nullptr;     // device status word written by bounded waits
     lbm_status sticky = LBM_OK;
     std::string err;
     KernelSet* ks = nullptr;
@@ -42,6 +46,8 @@ struct lbm_handle {
     std::vector<void*> allocations;
 
     bool aa() const { return p.scheme == LBM_STREAM_AA; }
+    // every population element index fits in 32 bits
+    bool idx32() const { return (unsigned long long)q * N < (1ull << 32); }
     bool fp64() const { return p.arith == LBM_ARITH_FP64; }
     int plane() const { return p.nx * p.ny; }
 
@@ -85,7 +91,10 @@ struct lbm_handle {
         return a;
     }
     int scheme_now() const { return !aa() ? lbm::SCHEME_AB : ((t & 1) ? lbm::SCHEME_AA_LOC : lbm::SCHEME_AA_PP); }
-    int layout_now() const { return !aa() ? lbm::LAYOUT_AB : ((t & 1) ? lbm::LAYOUT_AA_NATURAL : lbm::LAYOUT_AA_SWAPPED); }
+    int layout_now() const {
+        if (aa()) return (t & 1) ? lbm::LAYOUT_AA_NATURAL : lbm::LAYOUT_AA_SWAPPED;
+        return chunked ? lbm::LAYOUT_AB_CHUNKED : lbm::LAYOUT_AB;
+    }
     Launch step_launch(cudaStream_t s) const {
         Launch L;
         L.block = dim3(bx, by, 1);

@@ -19,16 +19,16 @@ namespace {
 using Real = std::conditional_t<LBM_ARITH == 1, double, float>;
 constexpr int FMT = LBM_FMT;
 
-template <class V, int COLL, int SCHEME, bool FLAGS>
+template <class V, int COLL, int SCHEME, bool FLAGS, class IX>
 cudaError_t launch_step(const void* args, const Launch& L) {
-    k_step<V, COLL, FMT, Real, SCHEME, FLAGS><<<L.grid, L.block, 0, L.stream>>>(
+    k_step<V, COLL, FMT, Real, SCHEME, FLAGS, IX><<<L.grid, L.block, 0, L.stream>>>(
         *static_cast<const StepArgs<Real>*>(args));
     return cudaGetLastError();
 }
 
-template <class V, int COLL, int SCHEME>
+template <class V, int COLL, int SCHEME, class IX>
 cudaError_t launch_ens(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
-    k_ensemble_step<V, COLL, FMT, Real, SCHEME><<<L.grid, L.block, 0, L.stream>>>(
+    k_ensemble_step<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
         static_cast<const EnsMember<Real>*>(members), tile_member, parity);
     return cudaGetLastError();
 }
@@ -40,30 +40,70 @@ cudaError_t launch_probe(const void* args, int mode, const Launch& L) {
     return cudaGetLastError();
 }
 
-template <class V, bool AA>
+template <class V, int PL>
 cudaError_t launch_put(const void* args, int setf, const Launch& L) {
-    k_put<V, FMT, Real, AA><<<L.grid, L.block, 0, L.stream>>>(
+    k_put<V, FMT, Real, PL><<<L.grid, L.block, 0, L.stream>>>(
         *static_cast<const PutArgs<Real>*>(args), setf);
+    return cudaGetLastError();
+}
+
+template <class V, int COLL, int NX>
+cudaError_t launch_staged(const void* args, int grid, int tiles_y, int* status, cudaStream_t stream) {
+    constexpr int smem = StagedShape<NX, FMT>::template smem_bytes<V>();
+    static bool configured = false;
+    if (!configured) {
+        const cudaError_t e = cudaFuncSetAttribute(k_step_staged<V, COLL, FMT, NX>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_step_staged<V, COLL, FMT, NX><<<grid, StagedShape<NX, FMT>::THREADS, smem, stream>>>(
+        *static_cast<const StepArgs<float>*>(args), tiles_y, status);
+    return cudaGetLastError();
+}
+
+template <class V, int COLL>
+cudaError_t launch_pair(const void* args, const Launch& L) {
+    k_step_pair<V, COLL, FMT><<<L.grid, L.block, 0, L.stream>>>(*static_cast<const StepArgs<float>*>(args));
+    return cudaGetLastError();
+}
+
+template <class V, int COLL>
+cudaError_t launch_pair_chunked(const void* args, const Launch& L) {
+    k_step_pair_chunked<V, COLL, FMT><<<L.grid, L.block, 0, L.stream>>>(*static_cast<const StepArgs<float>*>(args));
     return cudaGetLastError();
 }
 
 template <class V, int COLL>
 void fill() {
     KernelSet& s = kernel_set(V::ID, COLL, FMT, LBM_ARITH);
-    s.step[SCHEME_AB][0] = launch_step<V, COLL, SCHEME_AB, false>;
-    s.step[SCHEME_AB][1] = launch_step<V, COLL, SCHEME_AB, true>;
-    s.step[SCHEME_AA_PP][0] = launch_step<V, COLL, SCHEME_AA_PP, false>;
-    s.step[SCHEME_AA_PP][1] = launch_step<V, COLL, SCHEME_AA_PP, true>;
-    s.step[SCHEME_AA_LOC][0] = launch_step<V, COLL, SCHEME_AA_LOC, false>;
-    s.step[SCHEME_AA_LOC][1] = launch_step<V, COLL, SCHEME_AA_LOC, true>;
-    s.ens[SCHEME_AB] = launch_ens<V, COLL, SCHEME_AB>;
-    s.ens[SCHEME_AA_PP] = launch_ens<V, COLL, SCHEME_AA_PP>;
-    s.ens[SCHEME_AA_LOC] = launch_ens<V, COLL, SCHEME_AA_LOC>;
+    static_for<0, 3>([&](auto SC) {
+        s.step[SC.value][0][0] = launch_step<V, COLL, SC.value, false, size_t>;
+        s.step[SC.value][1][0] = launch_step<V, COLL, SC.value, true, size_t>;
+        s.step[SC.value][0][1] = launch_step<V, COLL, SC.value, false, uint32_t>;
+        s.step[SC.value][1][1] = launch_step<V, COLL, SC.value, true, uint32_t>;
+        s.ens[SC.value][0] = launch_ens<V, COLL, SC.value, size_t>;
+        s.ens[SC.value][1] = launch_ens<V, COLL, SC.value, uint32_t>;
+    });
     s.probe[LAYOUT_AB] = launch_probe<V, LAYOUT_AB>;
     s.probe[LAYOUT_AA_SWAPPED] = launch_probe<V, LAYOUT_AA_SWAPPED>;
     s.probe[LAYOUT_AA_NATURAL] = launch_probe<V, LAYOUT_AA_NATURAL>;
-    s.put[0] = launch_put<V, false>;
-    s.put[1] = launch_put<V, true>;
+    s.probe[LAYOUT_AB_CHUNKED] = launch_probe<V, LAYOUT_AB_CHUNKED>;
+    s.put[0] = launch_put<V, 0>;
+    s.put[1] = launch_put<V, 1>;
+    s.put[2] = launch_put<V, 2>;
+    if constexpr (LBM_ARITH == 0 && FMT >= 2) {
+        s.pair = launch_pair<V, COLL>;
+        s.pair_chunked = launch_pair_chunked<V, COLL>;
+    }
+    if constexpr (LBM_ARITH == 0 && FMT != 0 && std::is_same<V, D3Q19>::value) {
+        s.staged[0] = launch_staged<V, COLL, 128>;
+        s.staged[1] = launch_staged<V, COLL, 256>;
+        s.staged[2] = launch_staged<V, COLL, 512>;
+        s.staged_rows[0] = StagedShape<128, FMT>::H;
+        s.staged_rows[1] = StagedShape<256, FMT>::H;
+        s.staged_rows[2] = StagedShape<512, FMT>::H;
+    }
     s.present = true;
 }
 

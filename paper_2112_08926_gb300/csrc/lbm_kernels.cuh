@@ -20,7 +20,17 @@
 namespace lbm {
 
 enum { SCHEME_AB = 0, SCHEME_AA_PP = 1, SCHEME_AA_LOC = 2 };
-enum { LAYOUT_AB = 0, LAYOUT_AA_SWAPPED = 1, LAYOUT_AA_NATURAL = 2 };
+enum { LAYOUT_AB = 0, LAYOUT_AA_SWAPPED = 1, LAYOUT_AA_NATURAL = 2, LAYOUT_AB_CHUNKED = 3 };
+
+// Chunked (array-of-structure-of-arrays) layout of a flag-free A-B lattice
+// with nx a multiple of 64: the cells of a row are cut into chunks of 64
+// consecutive x; chunk c = n / 64 stores its q populations one after the
+// other, 64 codes each.  Element of population i of cell n:
+constexpr int CHUNK = 64;
+template <class V>
+__host__ __device__ __forceinline__ uint32_t chunk_elem(int i, uint32_t n) {
+    return ((n >> 6) * (uint32_t)V::Q + (uint32_t)i) * CHUNK + (n & (CHUNK - 1));
+}
 enum { PROBE_FIELDS = 0, PROBE_F = 1, PROBE_REDUCE = 2 };
 
 // internal flag bits of non-solid cells, set by the library after upload:
@@ -79,11 +89,11 @@ __device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t
 // cell beside it, or bounce-back if that cell is solid too.  Addresses are
 // chosen with selects and all loads are issued before the moving-wall terms
 // are added, so the loads stay in flight together.
-template <class V, int FMT, class R, bool AA>
+template <class V, int FMT, class R, bool AA, class IX>
 __device__ __forceinline__ void gather_boundary(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
                                                 const Nbr& nb, R* f) {
     using S = Storage<FMT>;
-    const size_t N = a.N;
+    const IX N = (IX)a.N;
     const uint32_t self = nb.self();
     uint32_t fy[V::Q];
     static_for<0, V::Q>([&](auto I) { fy[I.value] = a.flags[nb.up<V, I.value>()]; });
@@ -93,7 +103,7 @@ __device__ __forceinline__ void gather_boundary(const StepArgs<R>& a, const type
         constexpr int bslot = AA ? i : opposite(i);
         const uint32_t j = nb.up<V, i>();
         const bool wall = fy[i] & F_WALL;
-        size_t addr = wall ? (size_t)bslot * N + self : (size_t)slot * N + j;
+        IX addr = wall ? (IX)bslot * N + self : (IX)slot * N + j;
         if constexpr (!AA) {
             constexpr int cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
             constexpr int m0 = mirror<V>(i, 0), m1 = mirror<V>(i, 1), m2 = mirror<V>(i, 2);
@@ -102,26 +112,26 @@ __device__ __forceinline__ void gather_boundary(const StepArgs<R>& a, const type
             const uint32_t j2 = nb.xo[axis == 0 ? 1 : 1 - cx] + nb.yo[axis == 1 ? 1 : 1 - cy] +
                                 nb.zo[axis == 2 ? 1 : 1 - cz];
             const uint32_t f2 = fs ? (uint32_t)a.flags[j2] : F_WALL;
-            if (!(f2 & F_WALL)) addr = (size_t)(axis == 0 ? m0 : (axis == 1 ? m1 : m2)) * N + j2;
+            if (!(f2 & F_WALL)) addr = (IX)(axis == 0 ? m0 : (axis == 1 ? m1 : m2)) * N + j2;
         }
         f[i] = S::template load_g<R>(src, addr);
     });
     static_for<0, V::Q>([&](auto I) {
         constexpr int i = I.value;
-        if (fy[i] & F_MOVING) f[i] = f[i] + moving_term<V, i, R, S::SL>(a.node_u, N, nb.up<V, i>());
+        if (fy[i] & F_MOVING) f[i] = f[i] + moving_term<V, i, R, S::SL>(a.node_u, a.N, nb.up<V, i>());
     });
 }
 
 // Streamed populations of cell n at (x,y,z) for the given memory layout.
 // Cells without solid neighbours (internal bit F_NEAR_SOLID clear) take the
 // plain pull, as in the flag-free kernel.
-template <class V, int FMT, class R, bool FLAGS, int LAYOUT>
+template <class V, int FMT, class R, bool FLAGS, int LAYOUT, class IX = size_t>
 __device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
                                        int x, int y, int z, uint32_t n, uint32_t fl, R* f) {
     using S = Storage<FMT>;
     if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {
         static_for<0, V::Q>([&](auto I) {
-            f[I.value] = S::template load_g<R>(src, (size_t)I.value * a.N + n);
+            f[I.value] = S::template load_g<R>(src, (IX)I.value * (IX)a.N + n);
         });
         if (FLAGS && (fl & F_NEAR_MOVING)) {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
@@ -130,29 +140,34 @@ __device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Stor
                 if (a.flags[j] & F_MOVING) f[I.value] = f[I.value] + moving_term<V, I.value, R, S::SL>(a.node_u, a.N, j);
             });
         }
+    } else if constexpr (LAYOUT == LAYOUT_AB_CHUNKED) {
+        const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
+        static_for<0, V::Q>([&](auto I) {
+            f[I.value] = S::template load_g<R>(src, chunk_elem<V>(I.value, nb.up<V, I.value>()));
+        });
     } else {
         constexpr bool AA = LAYOUT == LAYOUT_AA_SWAPPED;
         if (FLAGS && (fl & F_NEAR_SOLID)) {
             int sx = x;
             if (!AA && (fl & F_OUTFLOW)) sx = x == 0 ? a.nx - 1 : x - 1;
             const Nbr nb(sx, y, z, a.nx, a.ny, a.nz);
-            gather_boundary<V, FMT, R, AA>(a, src, nb, f);
+            gather_boundary<V, FMT, R, AA, IX>(a, src, nb, f);
         } else {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
             static_for<0, V::Q>([&](auto I) {
                 constexpr int slot = AA ? opposite(I.value) : I.value;
-                f[I.value] = S::template load_g<R>(src, (size_t)slot * a.N + nb.up<V, I.value>());
+                f[I.value] = S::template load_g<R>(src, (IX)slot * (IX)a.N + nb.up<V, I.value>());
             });
         }
     }
 }
 
 // One fused stream-collide update of cell (x, y, z).
-template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS>
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
 __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, int z) {
     using S = Storage<FMT>;
     using T = typename S::T;
-    const size_t N = a.N;
+    const IX N = (IX)a.N;
     const uint32_t n = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
@@ -163,19 +178,19 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     }
     R f[V::Q];
     if (FLAGS && (fl & F_EQ)) {
-        const R u[3] = {(R)a.node_u[n], (R)a.node_u[N + n], (R)a.node_u[2 * N + n]};
+        const R u[3] = {(R)a.node_u[n], (R)a.node_u[(size_t)a.N + n], (R)a.node_u[2 * (size_t)a.N + n]};
         equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f);
     } else {
         constexpr int LAYOUT = SCHEME == SCHEME_AB ? LAYOUT_AB
                              : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
-        gather<V, FMT, R, FLAGS, LAYOUT>(a, src, x, y, z, n, fl, f);
+        gather<V, FMT, R, FLAGS, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
         collide<V, COLL, R, S::SL>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
-        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(dst, (size_t)I.value * N + n, f[I.value]); });
+        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(dst, (IX)I.value * N + n, f[I.value]); });
     } else if constexpr (SCHEME == SCHEME_AA_LOC) {
         static_for<0, V::Q>([&](auto I) {
-            S::template store_g<R>(dst, (size_t)opposite(I.value) * N + n, f[I.value]);
+            S::template store_g<R>(dst, (IX)opposite(I.value) * N + n, f[I.value]);
         });
     } else {
         const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
@@ -184,22 +199,294 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
                 constexpr int i = I.value;
                 const uint32_t d = nb.down<V, i>();
                 const bool wall = a.flags[d] & F_WALL;   // reflected back into this cell
-                S::template store_g<R>(dst, wall ? (size_t)opposite(i) * N + n : (size_t)i * N + d, f[i]);
+                S::template store_g<R>(dst, wall ? (IX)opposite(i) * N + n : (IX)i * N + d, f[i]);
             });
         } else {
             static_for<0, V::Q>([&](auto I) {
-                S::template store_g<R>(dst, (size_t)I.value * N + nb.down<V, I.value>(), f[I.value]);
+                S::template store_g<R>(dst, (IX)I.value * N + nb.down<V, I.value>(), f[I.value]);
             });
         }
     }
 }
 
-template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS>
+// IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic)
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
 __global__ void __launch_bounds__(256) k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    cell_step<V, COLL, FMT, R, SCHEME, FLAGS>(a, x, y, (int)blockIdx.z);
+    cell_step<V, COLL, FMT, R, SCHEME, FLAGS, IX>(a, x, y, (int)blockIdx.z);
+}
+
+// ---------------------------------------------------------------- staged kernel
+// Flag-free periodic A-B step with the source rows staged in shared memory by
+// the bulk-copy engine.  A persistent CTA of NX*H threads walks tiles of H
+// whole x-rows (one z-plane); for every tile, warp 0 issues one
+// cp.async.bulk per (population, row) -- the row (y - c_y, z - c_z) of
+// population i, exactly the cells that stream into the tile -- completing on
+// the stage's mbarrier.  STAGES tiles are in flight while one is computed,
+// so the bytes in flight do not depend on registers.  Each population load
+// is then one shared-memory read at a constant offset (x-wrap by selecting
+// x-1, x or x+1); the per-cell arithmetic is cell_step's.  Every wait is
+// bounded: on timeout the kernel writes *status = 1 and returns.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// bounded wait: about a second of polling before giving up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    for (uint32_t k = 0; k < (1u << 22); ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int NX, int FMT> struct StagedShape {
+    using T = typename Storage<FMT>::T;
+    static constexpr int THREADS = 512;
+    static constexpr int H = THREADS / NX;              // rows per tile
+    static constexpr int ROW = NX * (int)sizeof(T);     // bytes per staged row
+    static constexpr int STAGES = sizeof(T) == 2 ? 3 : 2;
+    template <class V> static constexpr int stage_bytes() { return V::Q * H * ROW; }
+    template <class V> static constexpr int smem_bytes() { return STAGES * stage_bytes<V>() + 8 * STAGES; }
+};
+
+template <class V, int COLL, int FMT, int NX>
+__global__ void __launch_bounds__(512, 2) k_step_staged(const StepArgs<float> a, int tiles_y, int* status) {
+    using S = Storage<FMT>;
+    using T = typename S::T;
+    using Sh = StagedShape<NX, FMT>;
+    constexpr int H = Sh::H, ROW = Sh::ROW, STAGES = Sh::STAGES;
+    constexpr int STAGE_BYTES = Sh::template stage_bytes<V>();
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int x = tid % NX, r = tid / NX;
+    const int ntiles = tiles_y * a.nz;
+    if ((int)blockIdx.x >= ntiles) return;
+    const int my = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const uint32_t N = a.N;
+    const uint32_t plane = (uint32_t)NX * (uint32_t)a.ny;
+    if (tid == 0) {
+        for (int st = 0; st < STAGES; ++st) mbar_init(&bars[st], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+
+    // warp 0 (all lanes compute the same addresses, lane 0 issues): stage tile k into buffer st
+    auto issue = [&](int k, int st) {
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        const int z = t / tiles_y, y0 = (t - z * tiles_y) * H;
+        if (lane == 0) mbar_expect_tx(&bars[st], STAGE_BYTES);
+        unsigned char* base = smem + st * STAGE_BYTES;
+        static_for<0, V::Q>([&](auto I) {
+            constexpr int i = I.value, cy = V::c(i, 1), cz = V::c(i, 2);
+            const int zs = z - cz < 0 ? a.nz - 1 : (z - cz >= a.nz ? 0 : z - cz);
+#pragma unroll
+            for (int rr = 0; rr < H; ++rr) {
+                // rows of a ragged last tile may lie past ny: any in-range row will do
+                int ys = y0 + rr - cy;
+                if (ys < 0) ys += a.ny;
+                while (ys >= a.ny) ys -= a.ny;
+                const T* src = (const T*)a.src + (i * N + (uint32_t)zs * plane + (uint32_t)ys * NX);
+                if (lane == 0) bulk_g2s(base + (i * H + rr) * ROW, src, ROW, &bars[st]);
+            }
+        });
+    };
+
+    if (warp == 0)
+        for (int k = 0; k < STAGES && k < my; ++k) issue(k, k);
+    const int xm = x == 0 ? NX - 1 : x - 1, xp = x == NX - 1 ? 0 : x + 1;
+    T* dst = (T*)a.dst;
+    for (int k = 0; k < my; ++k) {
+        const int st = k % STAGES;
+        if (!mbar_wait(&bars[st], (uint32_t)((k / STAGES) & 1))) {
+            if (lane == 0) atomicExch(status, 1);
+            return;
+        }
+        const int t = (int)blockIdx.x + k * (int)gridDim.x;
+        const int z = t / tiles_y, y = (t - z * tiles_y) * H + r;
+        if (y < a.ny) {
+            const T* tile = (const T*)(smem + st * STAGE_BYTES) + r * NX;
+            float f[V::Q];
+            static_for<0, V::Q>([&](auto I) {
+                constexpr int i = I.value, cx = V::c(i, 0);
+                const int xs = cx == 0 ? x : (cx > 0 ? xm : xp);
+                f[i] = S::template load_g<float>(tile, (uint32_t)(i * H * NX + xs));
+            });
+            collide<V, COLL, float, S::SL>(a.k, f);
+            const uint32_t n = (uint32_t)z * plane + (uint32_t)y * NX + x;
+            static_for<0, V::Q>([&](auto I) { S::template store_g<float>(dst, (uint32_t)I.value * N + n, f[I.value]); });
+        }
+        __syncthreads();
+        if (warp == 0 && k + STAGES < my) issue(k + STAGES, st);
+    }
+}
+
+// ---------------------------------------------------------------- paired kernel
+// Flag-free periodic A-B step for 16-bit storage with two x-neighbouring
+// cells per thread: every population is read and written as one 32-bit pair
+// of codes.  A pair shifted by one cell in x (c_x != 0) is assembled from the
+// thread's own aligned pair and the neighbouring lane's (warp shuffle); at the
+// end of a warp and at the periodic wrap the missing code is read directly.
+// Needs nx even, q*N < 2^32 and a block width that is a multiple of 32 (a warp
+// then covers one row segment).  Per-cell arithmetic is cell_step's.
+template <class V, int COLL, int FMT>
+__global__ void __launch_bounds__(256, 3) k_step_pair(const StepArgs<float> a) {
+    using C = Codec16<FMT>;
+    constexpr int SL = C::SL;
+    const int px = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    const int lane = threadIdx.x & 31;
+    const bool active = (2 * px < a.nx) && (y < a.ny);
+    // inactive threads stay for the shuffles, reading a valid pair
+    const int x0 = active ? 2 * px : 0;
+    const int yc = y < a.ny ? y : 0;
+    const uint32_t nx = (uint32_t)a.nx, plane = nx * (uint32_t)a.ny, N = a.N;
+    const uint32_t yo[3] = {(uint32_t)(yc == 0 ? a.ny - 1 : yc - 1) * nx, (uint32_t)yc * nx,
+                            (uint32_t)(yc == a.ny - 1 ? 0 : yc + 1) * nx};
+    const uint32_t zo[3] = {(uint32_t)(z == 0 ? a.nz - 1 : z - 1) * plane, (uint32_t)z * plane,
+                            (uint32_t)(z == a.nz - 1 ? 0 : z + 1) * plane};
+    const uint32_t xm = x0 == 0 ? nx - 1 : (uint32_t)x0 - 1;        // source of x0 when c_x = +1
+    const uint32_t xp2 = (uint32_t)x0 + 2 == nx ? 0 : (uint32_t)x0 + 2; // source of x0+1 when c_x = -1
+    const bool edge_lo = lane == 0 || x0 == 0;
+    const bool edge_hi = lane == 31 || (uint32_t)x0 + 2 == nx;
+    const uint16_t* src = (const uint16_t*)a.src;
+    uint32_t g[V::Q];   // lo half: cell x0, hi half: cell x0 + 1
+    static_for<0, V::Q>([&](auto I) {
+        constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
+        const uint32_t row = (uint32_t)i * N + yo[1 - cy] + zo[1 - cz];
+        const uint32_t P = *reinterpret_cast<const uint32_t*>(src + row + (uint32_t)x0);
+        if constexpr (cx == 0) {
+            g[i] = P;
+        } else if constexpr (cx > 0) {      // sources x0-1, x0
+            const uint32_t Pu = __shfl_up_sync(0xffffffffu, P, 1);
+            const uint32_t e = edge_lo ? (uint32_t)src[row + xm] : (Pu >> 16);
+            g[i] = (P << 16) | e;
+        } else {                            // sources x0+1, x0+2
+            const uint32_t Pd = __shfl_down_sync(0xffffffffu, P, 1);
+            const uint32_t e = edge_hi ? (uint32_t)src[row + xp2] : (Pd & 0xFFFFu);
+            g[i] = (P >> 16) | (e << 16);
+        }
+    });
+    float f[V::Q];
+    static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] & 0xFFFFu); });
+    collide<V, COLL, float, SL>(a.k, f);
+    static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFF0000u) | C::enc_g(f[I.value]); });
+    static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] >> 16); });
+    collide<V, COLL, float, SL>(a.k, f);
+    static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFFu) | (C::enc_g(f[I.value]) << 16); });
+    if (active) {
+        uint16_t* dst = (uint16_t*)a.dst;
+        const uint32_t n0 = (uint32_t)x0 + yo[1] + zo[1];
+        static_for<0, V::Q>([&](auto I) {
+            *reinterpret_cast<uint32_t*>(dst + (uint32_t)I.value * N + n0) = g[I.value];
+        });
+    }
+}
+
+// Pairs of codes: FP16 and FP16S convert two values per instruction.
+template <int FMT> struct PairCodec {
+    __device__ static float2 dec(uint32_t g) {
+        return make_float2(Codec16<FMT>::dec_g(g & 0xFFFFu), Codec16<FMT>::dec_g(g >> 16));
+    }
+    __device__ static uint32_t enc(float lo, float hi) {
+        return Codec16<FMT>::enc_g(lo) | (Codec16<FMT>::enc_g(hi) << 16);
+    }
+};
+template <int FMT> struct PairCodecHalf {
+    __device__ static float2 dec(uint32_t g) {
+        __half2 h;
+        memcpy(&h, &g, 4);
+        return __half22float2(h);
+    }
+    __device__ static uint32_t enc(float lo, float hi) {   // round to nearest even, as __float2half_rn
+        const __half2 h = __floats2half2_rn(lo, hi);
+        uint32_t g;
+        memcpy(&g, &h, 4);
+        return g;
+    }
+};
+template <> struct PairCodec<2> : PairCodecHalf<2> {};
+template <> struct PairCodec<3> : PairCodecHalf<3> {};
+
+// Flag-free periodic A-B step on the chunked layout, 16-bit storage: a warp
+// owns one 64-cell chunk of a row (lane l: cells 2l and 2l+1) and moves every
+// population as one 128-byte line of 32-bit code pairs, at a compile-time
+// offset from the chunk of the source row.  Pairs shifted in x are assembled
+// by warp shuffles; lanes 0 and 31 read the missing code from the
+// neighbouring chunk (periodic in x).  Block = 32 x by threads; needs nx a
+// multiple of 64 and q*N < 2^32.  Per-cell arithmetic is cell_step's.
+template <class V, int COLL, int FMT>
+__global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<float> a) {
+    using PC = PairCodec<FMT>;
+    constexpr int SL = Codec16<FMT>::SL;
+    constexpr uint32_t CHE = (uint32_t)V::Q * CHUNK;     // codes per chunk
+    const int lane = threadIdx.x;
+    const uint32_t X = blockIdx.x, XT = (uint32_t)a.nx / CHUNK;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (y >= a.ny) return;                                 // whole warps leave together
+    const uint32_t ny = (uint32_t)a.ny;
+    const uint32_t ry[3] = {(uint32_t)(y == 0 ? a.ny - 1 : y - 1), (uint32_t)y, (uint32_t)(y == a.ny - 1 ? 0 : y + 1)};
+    const uint32_t rz[3] = {(uint32_t)(z == 0 ? a.nz - 1 : z - 1) * ny, (uint32_t)z * ny,
+                            (uint32_t)(z == a.nz - 1 ? 0 : z + 1) * ny};
+    // chunk offsets of the x-neighbouring chunks (periodic)
+    const int32_t prev = X == 0 ? (int32_t)((XT - 1) * CHE) : -(int32_t)CHE;
+    const int32_t next = X == XT - 1 ? -(int32_t)((XT - 1) * CHE) : (int32_t)CHE;
+    const uint16_t* src = (const uint16_t*)a.src;
+    // lane 0 reads code 63 of the previous chunk, lane 31 code 0 of the next one
+    const int32_t adj = lane == 0 ? prev + (CHUNK - 1) : next;
+    uint32_t g[V::Q];   // lo half: cell 2*lane, hi half: cell 2*lane + 1 (of this chunk)
+    // loads grouped by source row (c_y, c_z): one 64-bit pointer per row, the
+    // population offsets i*CHUNK are compile-time
+    static_for<0, 9>([&](auto RC) {
+        constexpr int cyr = RC.value % 3 - 1, czr = RC.value / 3 - 1;
+        const uint16_t* rowp = src + ((ry[1 - cyr] + rz[1 - czr]) * XT + X) * CHE;
+        const uint32_t* pairs = reinterpret_cast<const uint32_t*>(rowp) + lane;
+        const uint16_t* edge = rowp + adj;
+        static_for<0, V::Q>([&](auto I) {
+            constexpr int i = I.value, cx = V::c(i, 0);
+            if constexpr (V::c(i, 1) == cyr && V::c(i, 2) == czr) {
+                const uint32_t P = pairs[i * (CHUNK / 2)];
+                if constexpr (cx == 0) {
+                    g[i] = P;
+                } else if constexpr (cx > 0) {      // sources 2l-1, 2l
+                    const uint32_t Pu = __shfl_up_sync(0xffffffffu, P, 1);
+                    const uint32_t e = lane == 0 ? (uint32_t)edge[i * CHUNK] : (Pu >> 16);
+                    g[i] = (P << 16) | e;
+                } else {                            // sources 2l+1, 2l+2
+                    const uint32_t Pd = __shfl_down_sync(0xffffffffu, P, 1);
+                    const uint32_t e = lane == 31 ? (uint32_t)edge[i * CHUNK] : (Pd & 0xFFFFu);
+                    g[i] = (P >> 16) | (e << 16);
+                }
+            }
+        });
+    });
+    float fa[V::Q], fb[V::Q];
+    static_for<0, V::Q>([&](auto I) { fa[I.value] = PC::dec(g[I.value]).x; });
+    collide<V, COLL, float, SL>(a.k, fa);
+    static_for<0, V::Q>([&](auto I) { fb[I.value] = PC::dec(g[I.value]).y; });
+    collide<V, COLL, float, SL>(a.k, fb);
+    uint32_t* out = reinterpret_cast<uint32_t*>((uint16_t*)a.dst + ((ry[1] + rz[1]) * XT + X) * CHE) + lane;
+    static_for<0, V::Q>([&](auto I) { out[I.value * (CHUNK / 2)] = PC::enc(fa[I.value], fb[I.value]); });
 }
 
 // ---------------------------------------------------------------- ensemble
@@ -220,7 +507,7 @@ template <class R> struct EnsMember {
     FastDiv by_plane, by_nx;
 };
 
-template <class V, int COLL, int FMT, class R, int SCHEME>
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
 __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
@@ -231,7 +518,7 @@ __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __res
     const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
     const uint32_t y = M.by_nx.div(r);
     const uint32_t x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, true>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- probes
@@ -332,8 +619,9 @@ template <class R> struct PutArgs {
     const double* in[4];
 };
 
-template <class V, int FMT, class R, bool AA>
+template <class V, int FMT, class R, int PUT_LAYOUT>   // 0: A-B, 1: A-A (swapped slots), 2: A-B chunked
 __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
+    constexpr bool AA = PUT_LAYOUT == 1;
     using S = Storage<FMT>;
     const StepArgs<R>& a = p.a;
     const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
@@ -353,7 +641,8 @@ __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
         }
         static_for<0, V::Q>([&](auto I) {
             constexpr int slot = AA ? opposite(I.value) : I.value;
-            S::template store<R>(dst, (size_t)slot * a.N + n, solid ? R(0) : f[I.value]);
+            const size_t e = PUT_LAYOUT == 2 ? (size_t)chunk_elem<V>(I.value, n) : (size_t)slot * a.N + n;
+            S::template store<R>(dst, e, solid ? R(0) : f[I.value]);
         });
     }
 }

@@ -16,12 +16,18 @@ using StepFn = cudaError_t (*)(const void* step_args, const Launch&);
 using EnsFn = cudaError_t (*)(const void* members, const uint32_t* tile_member, int parity, const Launch&);
 using ProbeFn = cudaError_t (*)(const void* probe_args, int mode, const Launch&);
 using PutFn = cudaError_t (*)(const void* put_args, int setf, const Launch&);
+// staged flag-free A-B step: grid size, tiles along y, status word
+using StagedFn = cudaError_t (*)(const void* step_args, int grid, int tiles_y, int* status, cudaStream_t);
 
 struct KernelSet {
-    StepFn step[3][2] = {};   // [scheme: AB, AA_PP, AA_LOC][flags]
-    EnsFn ens[3] = {};        // [scheme], flags always on
-    ProbeFn probe[3] = {};    // [layout: AB, AA swapped, AA natural]
-    PutFn put[2] = {};        // [A-A]
+    StepFn step[3][2][2] = {};   // [scheme: AB, AA_PP, AA_LOC][flags][32-bit indices]
+    EnsFn ens[3][2] = {};        // [scheme][32-bit indices], flags always on
+    ProbeFn probe[4] = {};    // [layout: AB, AA swapped, AA natural, AB chunked]
+    PutFn put[3] = {};        // [A-B, A-A, A-B chunked]
+    StagedFn staged[3] = {};  // row length 128, 256, 512 (D3Q19, FP32 arithmetic only)
+    int staged_rows[3] = {};  // rows per tile
+    StepFn pair = nullptr;    // two cells per thread (flag-free A-B, 16-bit storage)
+    StepFn pair_chunked = nullptr;   // the same on the chunked layout
     bool present = false;
 };
 

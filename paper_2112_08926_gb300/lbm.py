@@ -30,6 +30,7 @@ STORAGES = {"FP64": 0, "FP32": 1, "FP16": 2, "FP16S": 3, "FP16C": 4,
             "P16_0S": 5, "P16_1S": 6, "P16_2C": 7, "P16_0": 8, "P16_1": 9}
 ARITHS = {"FP32": 0, "FP64": 1}
 SCHEMES = {"AB": 0, "AA": 1}
+VARIANTS = {"auto": 0, "generic": 1, "staged": 2, "paired": 3}
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 WALL, MOVING, EQ, OUTFLOW, FREESLIP = 0x01, 0x02, 0x04, 0x08, 0x10
 EXPORTS = [
@@ -39,7 +40,7 @@ EXPORTS = [
     "lbm_codec_encode", "lbm_codec_decode", "lbm_codec_encode_bits",
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_step_each",
     "lbm_ensemble_set_block", "lbm_ensemble_autotune", "lbm_ensemble_destroy",
-    "lbm_ensemble_last_error",
+    "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant",
 ]
 
 
@@ -71,7 +72,7 @@ class lbm_info(ctypes.Structure):
     _fields_ = [
         ("q", ctypes.c_int), ("cells", ctypes.c_int64), ("step", ctypes.c_int64),
         ("bytes_per_population", ctypes.c_int), ("has_flags", ctypes.c_int),
-        ("device_bytes", ctypes.c_size_t), ("ddf", ctypes.c_void_p * 2),
+        ("device_bytes", ctypes.c_size_t), ("ddf", ctypes.c_void_p * 2), ("layout", ctypes.c_int),
     ]
 
 
@@ -115,6 +116,8 @@ def load() -> ctypes.CDLL:
             "lbm_ensemble_set_block": [P, I, I],
             "lbm_ensemble_autotune": [P, I, pI, pI],
             "lbm_ensemble_destroy": [P],
+            "lbm_set_variant": [P, I],
+            "lbm_get_variant": [P],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -300,6 +303,13 @@ class Lattice:
         bx, by = ctypes.c_int(), ctypes.c_int()
         self._c(self._L.lbm_autotune(self._h, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)))
         return bx.value, by.value
+
+    def set_variant(self, variant: str):
+        """'auto', 'generic', 'staged' or 'paired' (see lbm_set_variant)."""
+        self._c(self._L.lbm_set_variant(self._h, VARIANTS[variant]))
+
+    def variant(self) -> str:
+        return {v: k for k, v in VARIANTS.items()}[self._L.lbm_get_variant(self._h)]
 
 
 class Ensemble:

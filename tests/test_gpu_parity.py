@@ -202,3 +202,103 @@ def test_autotune_keeps_results():
     g1, done = res[1]
     g0.step(done)
     assert np.array_equal(g0.f(), g1.f())
+
+
+@pytest.mark.parametrize("shape", [(3, 9, 128), (2, 6, 256), (2, 3, 512), (1, 1, 128), (1, 2, 256)])
+@pytest.mark.parametrize("storage", ["FP32", "FP16S", "FP16C", "P16_1S", "P16_2C"])
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+def test_staged_kernel_bitwise(shape, storage, coll):
+    nz, ny, nx = shape
+    fields = W.random_fields(shape, 17)
+    g = P().Lattice(nx, ny, nz, "D3Q19", coll, storage, "FP32", "AB", tau=0.57, trt_lambda=0.2)
+    g.set_variant("staged")
+    assert g.variant() == "staged"
+    g.set_rho_u(*fields)
+    g.step(7)
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", coll, "ORD32", storage, tau=0.57, trt_lambda=0.2)
+    o.set_rho_u(*fields)
+    o.step(7)
+    assert np.array_equal(g.f(), o.f())
+
+
+@pytest.mark.parametrize("vs,shape,block", [
+    ("D3Q19", (3, 9, 128), (32, 4)), ("D3Q19", (2, 5, 70), (32, 8)), ("D3Q19", (2, 3, 2), (32, 1)),
+    ("D3Q19", (1, 3, 198), (64, 2)), ("D2Q9", (1, 17, 132), (32, 8)), ("D3Q27", (3, 4, 66), (32, 4)),
+])
+@pytest.mark.parametrize("storage", ["FP16", "FP16S", "FP16C", "P16_0S", "P16_1S", "P16_2C", "P16_0", "P16_1"])
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+def test_paired_kernel_bitwise(vs, shape, block, storage, coll):
+    nz, ny, nx = shape
+    fields = W.random_fields(shape, 19)
+    force = (1e-5, -1e-5, 0.0) if coll == "TRT" else (0.0, 0.0, 0.0)
+    g = P().Lattice(nx, ny, nz, vs, coll, storage, "FP32", "AB", tau=0.61, trt_lambda=0.2, force=force)
+    g.set_block(*block)
+    g.set_variant("paired")
+    assert g.variant() == "paired"
+    g.set_rho_u(*fields)
+    g.step(5)
+    o = oracle.Lattice(nx, ny, nz, vs, coll, "ORD32", storage, tau=0.61, trt_lambda=0.2, force=force)
+    o.set_rho_u(*fields)
+    o.step(5)
+    assert np.array_equal(g.f(), o.f())
+
+
+@pytest.mark.parametrize("vs,shape", [("D3Q19", (3, 5, 128)), ("D3Q19", (2, 3, 64)), ("D3Q19", (1, 9, 192)),
+                                      ("D2Q9", (1, 11, 128)), ("D3Q27", (2, 3, 64))])
+@pytest.mark.parametrize("storage", ["FP16", "FP16S", "FP16C", "P16_0S", "P16_1S", "P16_2C", "P16_0", "P16_1"])
+@pytest.mark.parametrize("coll", ["SRT", "TRT"])
+def test_chunked_layout_bitwise(vs, shape, storage, coll):
+    nz, ny, nx = shape
+    fields = W.random_fields(shape, 23)
+    force = (2e-5, 1e-5, 0.0) if coll == "SRT" else (0.0, 0.0, 0.0)
+    g = P().Lattice(nx, ny, nz, vs, coll, storage, "FP32", "AB", tau=0.59, trt_lambda=0.2, force=force)
+    g.set_rho_u(*fields)
+    assert g.info().layout == 1 and g.variant() == "paired"
+    g.step(6)
+    o = oracle.Lattice(nx, ny, nz, vs, coll, "ORD32", storage, tau=0.59, trt_lambda=0.2, force=force)
+    o.set_rho_u(*fields)
+    o.step(6)
+    assert np.array_equal(g.f(), o.f())
+    r1, r2 = g.rho_u(), o.rho_u()
+    for a, b in zip(r1, r2):
+        assert np.array_equal(a, b)
+    # switching kernels converts the layout without changing a value
+    g.set_variant("generic")
+    assert g.info().layout == 0
+    g.step(3)
+    o.step(3)
+    assert np.array_equal(g.f(), o.f())
+    g.set_variant("auto")
+    assert g.info().layout == 1
+    g.step(2)
+    o.step(2)
+    assert np.array_equal(g.f(), o.f())
+
+
+def test_chunked_lattice_takes_flags_later():
+    shape = (3, 4, 64)
+    fields = W.random_fields(shape, 29)
+    geo = W.random_geometry(shape, 30)
+    g = P().Lattice(64, 4, 3, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=0.7)
+    g.set_rho_u(*fields)
+    assert g.info().layout == 1
+    g.step(4)
+    o = oracle.Lattice(64, 4, 3, "D3Q19", "SRT", "ORD32", "FP16S", tau=0.7)
+    o.set_rho_u(*fields)
+    o.step(4)
+    g.set_geometry(*geo)
+    o.set_geometry(*geo)
+    assert g.info().layout == 0
+    g.step(5)
+    o.step(5)
+    assert np.array_equal(g.f(), o.f())
+    g.set_f(o.f())
+    o.set_f(o.f())
+    g.set_geometry(None)
+    o.set_geometry(None)
+    g.set_f(o.f())
+    o.set_f(o.f())
+    assert g.info().layout == 1
+    g.step(3)
+    o.step(3)
+    assert np.array_equal(g.f(), o.f())
