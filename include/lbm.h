@@ -134,6 +134,25 @@ lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
  * of N doubles (any may be NULL).  Synchronises the stream. */
 lbm_status lbm_get_rho_u(lbm_handle* h, double* rho, double* ux, double* uy, double* uz);
 
+/* lbm_get_rho_u without any device allocation (the paper has no counterpart;
+ * this is a service for callers that cannot allocate).  lbm_get_rho_u takes
+ * a staging buffer from the lattice's allocator for the length of the call;
+ * a caller whose device memory is already fully used by the simulation, or
+ * that must not call cudaMalloc (it blocks the device and competes with a
+ * framework's memory pool), can use this entry point instead.  It writes the
+ * same values, staging through one fixed array of 2^20 doubles (8 MiB) that
+ * the library reserves on every GPU it is loaded on until the process exits.
+ * Limit: nx*ny <= 262144 cells (four doubles per cell of one xy-plane must
+ * fit); larger planes give LBM_ERR_UNSUPPORTED with the reason in
+ * lbm_last_error.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress), so make it before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (lattices on
+ * different streams read out at the same time) race and must be serialised
+ * by the caller.  Every chunk is written completely before it is read, so no
+ * state carries over between calls.  Host arrays as for lbm_get_rho_u;
+ * synchronises the lattice's stream. */
+lbm_status lbm_get_rho_u_static(lbm_handle* h, double* rho, double* ux, double* uy, double* uz);
+
 /* Streamed populations f_i(x) (shifted, decoded, exactly as the next
  * collision reads them) into a host array of q*N doubles; solid cells 0. */
 lbm_status lbm_get_f(lbm_handle* h, double* f);

@@ -40,7 +40,7 @@ EXPORTS = [
     "lbm_codec_encode", "lbm_codec_decode", "lbm_codec_encode_bits",
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_step_each",
     "lbm_ensemble_set_block", "lbm_ensemble_autotune", "lbm_ensemble_destroy",
-    "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant",
+    "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant", "lbm_get_rho_u_static",
 ]
 
 
@@ -101,6 +101,7 @@ def load() -> ctypes.CDLL:
             "lbm_set_rho_u": [P, P, P, P, P],
             "lbm_step": [P, I64],
             "lbm_get_rho_u": [P, P, P, P, P],
+            "lbm_get_rho_u_static": [P, P, P, P, P],
             "lbm_get_f": [P, P],
             "lbm_set_f": [P, P],
             "lbm_reduce": [P, pD, pD],

@@ -1,0 +1,68 @@
+"""The allocation-free field readback, lbm_get_rho_u_static, against
+lbm_get_rho_u (which stages through memory from the lattice's allocator).
+
+It serves callers that cannot allocate device memory while they read out a
+simulation (a lattice that fills the GPU, or a process whose memory pool
+belongs to another framework).  Called through the C ABI twice in a row, with
+a step in between so that the shared static array holds the previous call's
+results when the second call starts; both calls must return exactly what
+lbm_get_rho_u returns.  Lattices whose xy-plane does not fit the static array
+are refused with LBM_ERR_UNSUPPORTED.  This file is collected last."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def _read(lib, g, fn):
+    out = [np.empty(g.N, dtype=np.float64) for _ in range(4)]
+    st = getattr(lib, fn)(g.handle, *[ctypes.c_void_p(a.ctypes.data) for a in out])
+    return st, [a.reshape(g.shape) for a in out]
+
+
+@pytest.mark.parametrize("storage,scheme,shape", [
+    ("FP16S", "AB", (150, 64, 64)),     # three chunks of the static array; chunked layout
+    ("FP32", "AA", (9, 23, 37)),        # flags, in-place streaming
+    ("FP64", "AB", (5, 6, 7)),
+])
+def test_static_readback_matches_allocating_readback(storage, scheme, shape):
+    import paper_2112_08926_gb300 as P
+    lib = P.load()
+    nz, ny, nx = shape
+    arith = "FP64" if storage == "FP64" else "FP32"
+    g = P.Lattice(nx, ny, nz, "D3Q19", "SRT", storage, arith, scheme, tau=0.7, force=(1e-5, 0.0, 0.0))
+    if storage != "FP16S":
+        g.set_geometry(*W.random_geometry(shape, 3, outflow=0.0, freeslip_frac=0.0))
+    g.set_rho_u(*W.random_fields(shape, 4))
+    for _ in range(2):
+        g.step(3)
+        st_ref, ref = _read(lib, g, "lbm_get_rho_u")
+        st, got = _read(lib, g, "lbm_get_rho_u_static")
+        assert st_ref == 0 and st == 0
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b)
+    g.close()
+
+
+def test_static_readback_refuses_planes_beyond_the_buffer():
+    import paper_2112_08926_gb300 as P
+    lib = P.load()
+    g = P.Lattice(1024, 257, 1, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=0.7)
+    g.set_rho_u()
+    st, _ = _read(lib, g, "lbm_get_rho_u_static")
+    assert st == 4
+    assert b"262144" in lib.lbm_last_error(g.handle)
+    g.close()
