@@ -334,7 +334,8 @@ def main():
                 b = 2 * 19 * pop_bytes(storage)
                 per_format[name] = {"mlups": N * steps / dt / 1e6, "gbs": b * N * steps / dt / 1e9,
                                     "frac_hbm": b * N * steps / dt / 1e9 / peak, "bytes_per_cell": b,
-                                    "roofline_mlups": peak * 1e3 / b, "steps": steps}
+                                    "roofline_mlups": peak * 1e3 / b, "steps": steps,
+                                    "variant": gg.variant(), "traffic": profiled_traffic(name)}
                 gg.close()
             variants = {}
             for v in ("generic", "paired", "staged"):

@@ -26,7 +26,7 @@
  *   P16_2C        asymmetric posit with 2 exponent bits covering only the
  *                 lower flank (Sec. 3.2.2), unscaled.
  *
- * Readings of the paper taken here (also listed in the design doc):
+ * Readings of the paper taken here:
  *   - codes whose 15 magnitude bits are all zero decode to +-0 for every
  *     posit format (the printed P16_0/P16_1 decoders would return
  *     -2^113 / -2^-30 for them, which no working simulation can have used);
