@@ -1,8 +1,9 @@
 """Benchmark of the fused D3Q19 stream-collide step on one or more GB300s.
 
 Workload (one bench "step" = one time step of the whole lattice): D3Q19 SRT
-3-D Taylor-Green vortex on a fully periodic 256^3 lattice (u0 = 0.05,
-tau = 0.53), initial fields from the closed form, A-B streaming, flag-free
+Taylor-Green vortex (the 2-D closed form of Sec. 4.2 extruded along z, an
+exact 3-D flow) on a fully periodic 256^3 lattice (u0 = 0.05, tau = 0.53),
+initial fields from the closed form at t = 0, A-B streaming, flag-free
 periodic kernel -- the paper's benchmark box (Sec. 5: periodic cube, no
 boundary nodes, 256^3).  The headline tier is FP32 arithmetic with FP16S
 storage (`--format`); every other storage tier is measured on the same
@@ -30,7 +31,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "D3Q19 MLUPs/s per storage format vs HBM roofline; ensemble MLUPs/s vs per-launch"
-PAPER_A100_FP16S = 15455.0   # MLUPs/s, Nvidia A100 40GB, FP32/FP16S, D3Q19 SRT 256^3 (Table 5)
+PAPER_A100_FP16S = 15455.0   # MLUPs/s, Nvidia A100 40GB, FP32/FP16S, D3Q19 SRT 256^3 (appendix hardware table, Table 6)
 TIERS = [  # (name, arithmetic, storage)
     ("FP64/FP64", "FP64", "FP64"), ("FP64/FP32", "FP64", "FP32"), ("FP32/FP32", "FP32", "FP32"),
     ("FP32/FP16", "FP32", "FP16"), ("FP32/FP16S", "FP32", "FP16S"), ("FP32/FP16C", "FP32", "FP16C"),
@@ -128,8 +129,9 @@ class ClockSampler:
 
 
 def tg_fields(n):
+    """Closed-form Taylor-Green vortex at t = 0 (Sec. 4.2), extruded along z."""
     import workloads as W
-    return W.taylor_green_3d(n, 0.05)
+    return W.taylor_green_extruded(n, 0.05)
 
 
 def make_lattice(P, n, arith, storage, scheme="AB", fields=None):
@@ -137,6 +139,21 @@ def make_lattice(P, n, arith, storage, scheme="AB", fields=None):
     if fields is not None:
         g.set_rho_u(*fields)
     return g
+
+
+def max_over_ranks(dist, seconds, device):
+    """The slowest rank's time (every rank gets it); `seconds` when not distributed."""
+    if dist is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(world, cells, steps, seconds):
+    """Whole-job throughput: every rank advances its own replica of `cells`."""
+    return world * cells * steps / seconds / 1e6
 
 
 def time_steps(torch, g, steps):
@@ -157,7 +174,7 @@ def cpu_baseline(n, storage, budget_s=10.0):
     import oracle
     import workloads as W
     o = oracle.Lattice(n, n, n, "D3Q19", "SRT", "ORD32", storage, tau=0.53)
-    o.set_rho_u(*W.taylor_green_3d(n, 0.05))
+    o.set_rho_u(*W.taylor_green_extruded(n, 0.05))
     t0 = time.perf_counter()
     o.step(1)
     t1 = time.perf_counter() - t0
@@ -219,7 +236,7 @@ def bench_reference(args, rank, world):
     import workloads as W
     n = 64
     o = oracle.Lattice(n, n, n, "D3Q19", "SRT", "ORD32", args.format, tau=0.53)
-    o.set_rho_u(*W.taylor_green_3d(n, 0.05))
+    o.set_rho_u(*W.taylor_green_extruded(n, 0.05))
     o.step(args.warmup)
     t0 = time.perf_counter()
     o.step(args.steps)
@@ -230,7 +247,8 @@ def bench_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"D3Q19 SRT Taylor-Green vortex, periodic, {args.size}^3 (sample {n}^3)",
+        "config": {"workload": f"D3Q19 SRT Taylor-Green vortex (2-D closed form extruded along z), "
+                               f"periodic {args.size}^3, u0=0.05, tau=0.53 (oracle sample {n}^3)",
                    "storage": args.format, "arithmetic": "FP32", "scheme": "AB"},
         "cpu_baseline": {"value": v, "unit": "MLUPs/s", "kind": "oracle", "cores": oracle.threads(),
                          "sample": f"each step one oracle step of a {n}^3 periodic D3Q19 SRT TGV lattice "
@@ -287,12 +305,9 @@ def main():
         gpu_id = str(local)
     with ClockSampler(gpu_id) as clk:
         elapsed = time_steps(torch, g, args.steps)
-    if dist:
-        t = torch.tensor([elapsed], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(dist, elapsed, "cuda")
     m1, e1 = g.reduce()
-    value = world * N * args.steps / elapsed / 1e6
+    value = job_mlups(world, N, args.steps, elapsed)
     ms = elapsed / args.steps * 1e3
     bpc = 2 * 19 * pop_bytes(args.format)
     peak, peak_kind = peaks()
@@ -314,12 +329,9 @@ def main():
     g.get_rho_u_ptr(*[o.data_ptr() for o in outs])
     torch.cuda.synchronize()
     e2e_t = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_t], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
+    e2e_t = max_over_ranks(dist, e2e_t, "cuda")
     g.close()
-    e2e = {"value": world * N * args.steps / e2e_t / 1e6, "unit": "MLUPs/s",
+    e2e = {"value": job_mlups(world, N, args.steps, e2e_t), "unit": "MLUPs/s",
            "h2d_bytes_per_step": 4 * N * 8 / args.steps, "d2h_bytes_per_step": 4 * N * 8 / args.steps}
 
     per_format, ens, cpu = None, None, None
@@ -368,9 +380,10 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPs/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": value / PAPER_A100_FP16S if args.format == "FP16S" else None,
-        "baseline_ref": "paper Table 5, Nvidia A100 40GB, FP32/FP16S, D3Q19 SRT 256^3: 15455 MLUPs/s",
+        "baseline_ref": "paper appendix hardware table (Table 6), Nvidia A100 40GB, FP32/FP16S, D3Q19 SRT 256^3: 15455 MLUPs/s",
         "dtype": "f32" if head_arith == "FP32" else "f64", "data": "synthetic",
-        "config": {"workload": f"D3Q19 SRT 3-D Taylor-Green vortex, periodic {n}^3, u0=0.05, tau=0.53",
+        "config": {"workload": f"D3Q19 SRT Taylor-Green vortex (2-D closed form extruded along z), "
+                               f"periodic {n}^3, u0=0.05, tau=0.53",
                    "storage": args.format, "arithmetic": head_arith, "scheme": args.scheme,
                    "kernel": "flag-free periodic", "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
