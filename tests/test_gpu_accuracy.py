@@ -1,0 +1,176 @@
+"""Accuracy of every storage tier on the paper's test systems.
+
+Each tier's velocity error is stated as a number (the bounds below are the
+measured values rounded up):
+  - plane Poiseuille 8x64x8 (tau 0.8, body force 1e-6, 10,000 steps):
+    relative L2 of u_x against the FP64 CPU oracle and against the analytic
+    start-up series (Sec. 4.1 error norm);
+  - 2-D Taylor-Green vortex extruded along z, 256^3 (u0 0.05, tau 0.53,
+    2000 steps): E/E0 against the closed form exp(-4 nu k^2 t) (Sec. 4.2) and
+    the velocity L2 against the GPU FP64 tier (itself within 1e-12 of the
+    FP64 oracle on smaller lattices);
+  - D2Q9 Taylor-Green, L = 256, u0 = 0.25, tau = 1 (Sec. 4.2): the kinetic
+    energy stops decaying at a plateau within a few decades of the square of
+    the storage format's truncation error (Table 2 epsilon).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import __graft_entry__
+import oracle
+import workloads as W
+from conftest import golden
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TIERS = [("FP64", "FP64"), ("FP64", "FP32"), ("FP32", "FP64"), ("FP32", "FP32"), ("FP32", "FP16"),
+         ("FP32", "FP16S"), ("FP32", "FP16C"), ("FP32", "P16_0S"), ("FP32", "P16_1S"), ("FP32", "P16_2C"),
+         ("FP32", "P16_0"), ("FP32", "P16_1")]
+
+# relative L2 bounds: (vs FP64 reference, vs analytic solution)
+POISEUILLE_BOUND = {
+    "FP64/FP64": (1e-12, 2e-4), "FP64/FP32": (2e-6, 2e-4), "FP32/FP64": (2e-5, 2e-4), "FP32/FP32": (2e-5, 2e-4),
+    "FP32/FP16": (0.3, 0.3), "FP32/FP16S": (0.3, 0.3), "FP32/FP16C": (0.15, 0.15), "FP32/P16_0S": (1.01, 1.01),
+    "FP32/P16_1S": (0.08, 0.08), "FP32/P16_2C": (0.5, 0.5), "FP32/P16_0": (1.01, 1.01), "FP32/P16_1": (1.01, 1.01),
+}
+TG_BOUND = {   # (|E/E0 / closed form - 1|, L2 of u vs FP64 tier)
+    "FP64/FP64": (5e-4, 1e-14), "FP64/FP32": (5e-4, 2e-7), "FP32/FP64": (5e-4, 1e-4), "FP32/FP32": (5e-4, 1e-4),
+    "FP32/FP16": (5e-4, 1.5e-3), "FP32/FP16S": (5e-4, 1e-3), "FP32/FP16C": (1e-3, 6e-4), "FP32/P16_0S": (1e-3, 4e-4),
+    "FP32/P16_1S": (1e-3, 4e-4), "FP32/P16_2C": (1e-3, 1.2e-3), "FP32/P16_0": (5e-3, 3e-2), "FP32/P16_1": (1e-3, 4e-3),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    __graft_entry__.build()
+
+
+def _pkg():
+    import paper_2112_08926_gb300 as P
+    return P
+
+
+def _startup_series(F, nu, H, eta, t, terms=400):
+    u = F / (2 * nu) * eta * (H - eta)
+    for n in range(1, 2 * terms, 2):
+        u -= 4 * F * H * H / (nu * math.pi ** 3 * n ** 3) * np.sin(n * math.pi * eta / H) * \
+            math.exp(-nu * n * n * math.pi ** 2 * t / (H * H))
+    return u
+
+
+def test_poiseuille_error_per_tier():
+    P = _pkg()
+    nx, ny, nz, tau, F, T = 8, 64, 8, 0.8, 1e-6, 10000
+    flags = W.poiseuille_plate(nx, ny, nz)
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "SRT", "DEF64", "FP64", tau=tau, force=(F, 0, 0))
+    o.set_geometry(flags)
+    o.set_rho_u()
+    o.step(T)
+    ref = o.rho_u()[1][:, 1:-1, :]
+    nu, H = (tau - 0.5) / 3, ny - 2
+    eta = np.arange(1, ny - 1) - 0.5
+    ana = _startup_series(F, nu, H, eta, T)[None, :, None] * np.ones_like(ref)
+    lines, errs = [], {}
+    for arith, storage in TIERS:
+        g = P.Lattice(nx, ny, nz, "D3Q19", "SRT", storage, arith, "AB", tau=tau, force=(F, 0, 0))
+        g.set_geometry(flags)
+        g.set_rho_u()
+        g.step(T)
+        ux = g.rho_u()[1][:, 1:-1, :]
+        g.close()
+        e_ref = np.linalg.norm(ux - ref) / np.linalg.norm(ref)
+        e_ana = np.linalg.norm(ux - ana) / np.linalg.norm(ana)
+        name = f"{arith}/{storage}"
+        lines.append(f"{name:12s} L2 vs FP64 oracle {e_ref:.3e}   vs analytic {e_ana:.3e}")
+        errs[name] = (e_ref, e_ana)
+    print("\nPoiseuille 8x64x8, 10000 steps\n" + "\n".join(lines))
+    for name, (e_ref, e_ana) in errs.items():
+        b_ref, b_ana = POISEUILLE_BOUND[name]
+        assert e_ref <= b_ref and e_ana <= b_ana, (name, e_ref, e_ana)
+
+
+def test_taylor_green_error_per_tier():
+    P = _pkg()
+    n, u0, tau, T = 256, 0.05, 0.53, 2000
+    fields = W.taylor_green_extruded(n, u0)
+    nu, k = (tau - 0.5) / 3, 2 * math.pi / n
+    closed = math.exp(-4 * nu * k * k * T)
+    ref_u = None
+    lines, errs = [], {}
+    for arith, storage in TIERS:
+        g = P.Lattice(n, n, n, "D3Q19", "SRT", storage, arith, "AB", tau=tau)
+        g.set_rho_u(*fields)
+        _, e0 = g.reduce()
+        g.step(T)
+        _, e1 = g.reduce()
+        _, ux, uy, _ = g.rho_u()
+        g.close()
+        u = np.stack([ux, uy])
+        if ref_u is None:
+            ref_u = u
+        e_E = abs(e1 / e0 / closed - 1)
+        e_u = np.linalg.norm(u - ref_u) / np.linalg.norm(ref_u)
+        name = f"{arith}/{storage}"
+        lines.append(f"{name:12s} |E/E0 / closed form - 1| {e_E:.3e}   L2 of u vs FP64 tier {e_u:.3e}")
+        errs[name] = (e_E, e_u)
+    print(f"\nTaylor-Green 256^3 extruded, {T} steps, closed-form E/E0 = {closed:.6f}\n" + "\n".join(lines))
+    for name, (e_E, e_u) in errs.items():
+        b_E, b_u = TG_BOUND[name]
+        assert e_E <= b_E and e_u <= b_u, (name, e_E, e_u)
+
+
+def _table2_eps():
+    eps = {"FP32": 2.0 ** -23, "FP64": 2.0 ** -52}
+    for row in golden("format_table2.txt"):
+        eps[row[0]] = float(row[1])
+    return eps
+
+
+def test_taylor_green_2d_energy_plateau():
+    """Sec. 4.2: E/E0 follows exp(-4 nu k^2 t) until it stalls at a plateau;
+    for the IEEE-like formats the plateau sits near the square of the storage
+    format's truncation error (Table 2)."""
+    P = _pkg()
+    eps = _table2_eps()
+    L, u0, tau = 256, 0.25, 1.0
+    nu, k = (tau - 0.5) / 3, 2 * math.pi / L
+    rate = 4 * nu * k * k
+    fields = W.taylor_green_extruded(L, u0, nz=1)
+    lines, plateaus, firsts = [], {}, {}
+    for arith, storage in TIERS:
+        g = P.Lattice(L, L, 1, "D2Q9", "SRT", storage, arith, "AB", tau=tau)
+        g.set_rho_u(*fields)
+        _, e0 = g.reduce()
+        hist, prev = [], e0
+        for _ in range(250):
+            g.step(1000)
+            _, e = g.reduce()
+            hist.append(e / e0)
+            if e > 0.9 * prev:      # decay has stopped
+                break
+            prev = e
+        g.close()
+        name = f"{arith}/{storage}"
+        plateaus[name] = hist[-1]
+        first = abs(hist[0] / math.exp(-rate * 1000) - 1)
+        lines.append(f"{name:12s} plateau E/E0 {hist[-1]:.3e} at {1000 * len(hist):6d} steps   "
+                     f"eps^2 {eps.get(storage, math.nan) ** 2:.2e}   first-1000-step decay vs closed form {first:.1e}")
+        firsts[name] = first
+    print("\nD2Q9 Taylor-Green L=256 u0=0.25 tau=1\n" + "\n".join(lines))
+    for name, first in firsts.items():
+        assert first < 0.05, (name, first)
+    # the plateau sits within a few decades of eps^2: about 1e-2 eps^2 for
+    # formats whose range fits the shifted populations (FP64, FP32, FP16S),
+    # about eps^2 for FP16, FP16C and the scaled posits
+    for name in ("FP64/FP64", "FP32/FP32", "FP32/FP16", "FP32/FP16S", "FP32/FP16C", "FP32/P16_1S", "FP32/P16_2C"):
+        e2 = eps[name.split("/")[1]] ** 2
+        assert 1e-3 * e2 < plateaus[name] < 1e1 * e2, name
+    # Sec. 4.2: P16_0S holds the populations outside its accurate interval
+    assert plateaus["FP32/P16_0S"] > 1e2 * eps["P16_0S"] ** 2
+    # Sec. 4.2: FP64 arithmetic with FP32 storage plateaus far below FP32 / FP32
+    assert plateaus["FP64/FP32"] < 1e-2 * plateaus["FP32/FP32"]
