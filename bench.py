@@ -229,6 +229,38 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
             "speedup": t_e / t_b, "launches_per_step": {"batched": 1, "per_launch": count}}
 
 
+def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1):
+    """D3Q19 TRT lid-driven cavities N^3 (wall shell included, lid z = N-1
+    moving along +y, rho = 1, u = 0 at start, tau from Re = u_lid (N-2) / nu):
+    FP32 storage up to 512^3, 16-bit up to 1024^3 (A-B below 768^3, in-place
+    A-A from 768^3 on).  Algorithmic bytes per cell: 2 q s + 1 (own flag)."""
+    import workloads as W
+    peak, _ = peaks()
+    rows = []
+    for storage in formats:
+        sizes = [64, 96, 128, 192, 256, 384, 512] + ([] if storage in ("FP32", "FP64") else [768, 1024])
+        for n in sizes:
+            scheme = "AA" if n >= 768 else "AB"
+            tau = 0.5 + 3.0 * u_lid * (n - 2) / re
+            g = P.Lattice(n, n, n, "D3Q19", "TRT", storage, "FP32", scheme, tau=tau)
+            g.set_geometry(W.cavity_flags(n))
+            g.set_nodes(*W.cavity_lid(n, u_lid))
+            g.set_rho_u()
+            g.step(5)
+            dt = time_steps(torch, g, steps)
+            m, e = g.reduce()
+            info = g.info()
+            g.close()
+            cells = n ** 3
+            b = 2 * 19 * pop_bytes(storage) + 1
+            rows.append({"storage": storage, "n": n, "scheme": scheme, "tau": tau, "steps": steps,
+                         "mlups": cells * steps / dt / 1e6, "gbs": b * cells * steps / dt / 1e9,
+                         "frac_hbm": b * cells * steps / dt / 1e9 / peak, "bytes_per_cell": b,
+                         "device_gb": info.device_bytes / 1e9, "kinetic_energy": e})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return rows
+
+
 def bench_reference(args, rank, world):
     if rank != 0:
         return
@@ -270,6 +302,8 @@ def main():
     ap.add_argument("--no-sweep", action="store_true", help="headline tier only")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cavity-sweep", action="store_true",
+                    help="only the D3Q19 TRT lid-driven cavity size sweep (one JSON line)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -287,6 +321,12 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2112_08926_gb300 as P
+
+    if args.cavity_sweep:
+        if rank == 0:
+            rows = cavity_sweep(P, torch, args.steps)
+            print(json.dumps({"cavity_sweep": rows, "peak_gbs": peaks()[0]}), flush=True)
+        return
 
     n = args.size
     N = n ** 3

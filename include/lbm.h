@@ -116,6 +116,19 @@ lbm_status lbm_destroy(lbm_handle* h);
 lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* node_u,
                             const float* node_rho);
 
+/* Boundary-node data of listed cells only, for lattices whose boundary is a
+ * small part of the domain (a 1024^3 cavity has 10^6 lid cells among 10^9):
+ * the wall velocity of MOVING cells (Sec. 4.4) and the state of EQ cells
+ * (Sec. 4.3) without full-size host arrays.  cells: `count` distinct indices
+ * in [0, N); node_u: 3*count floats, component-major (ux[count], uy[count],
+ * uz[count]), or NULL to leave velocities unchanged; node_rho: count floats
+ * or NULL.  Cells not listed keep their values (zero velocity, unit density
+ * after lbm_set_geometry without node arrays).  Needs flags set by
+ * lbm_set_geometry.  Takes effect from the next step.  Errors: LBM_ERR_ARG
+ * (no flags, index out of range, an index listed twice), LBM_ERR_OOM. */
+lbm_status lbm_set_nodes(lbm_handle* h, int64_t count, const int64_t* cells, const float* node_u,
+                         const float* node_rho);
+
 /* Initialise every non-solid cell with the shifted equilibrium (Sec. 2.2)
  * of the given density and velocity (host arrays of N doubles; NULL means
  * rho = 1 / u = 0), converted to the arithmetic precision first; solid cells
@@ -156,6 +169,16 @@ lbm_status lbm_get_rho_u_static(lbm_handle* h, double* rho, double* ux, double* 
 /* Streamed populations f_i(x) (shifted, decoded, exactly as the next
  * collision reads them) into a host array of q*N doubles; solid cells 0. */
 lbm_status lbm_get_f(lbm_handle* h, double* f);
+
+/* Point probes: the streamed populations (as lbm_get_f) of `count` listed
+ * cells into f, population-major (f[i*count + k] for the k-th listed cell),
+ * and the density and velocity (as lbm_get_rho_u) of listed cells into
+ * arrays of `count` doubles (any may be NULL).  cells: host array of indices
+ * in [0, N), repeats allowed.  Errors: LBM_ERR_ARG (index out of range,
+ * NULL arrays), LBM_ERR_OOM.  Synchronise the stream. */
+lbm_status lbm_get_f_cells(lbm_handle* h, int64_t count, const int64_t* cells, double* f);
+lbm_status lbm_get_rho_u_cells(lbm_handle* h, int64_t count, const int64_t* cells, double* rho, double* ux,
+                               double* uy, double* uz);
 
 /* Overwrite the post-collision populations (what every cell streams out at
  * the next step) from a host array of q*N doubles, encoded to the storage

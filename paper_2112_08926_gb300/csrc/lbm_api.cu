@@ -1,6 +1,7 @@
 // Host implementation of the C ABI declared in include/lbm.h.
 // Validates arguments, owns device memory through the caller's allocator,
 // moves data in bounded chunks and launches the kernels of lbm_kernels.cuh.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -82,6 +83,33 @@ struct Staging {
     }
     bool ok() const { return h->scratch != nullptr; }
 };
+
+// Device buffer from the lattice's allocator, released (after the stream has
+// drained) when the call returns.
+struct TempBuffer {
+    lbm_handle* h;
+    size_t bytes;
+    void* p = nullptr;
+    TempBuffer(lbm_handle* hh, size_t b) : h(hh), bytes(b) { p = h->alloc(bytes); }
+    ~TempBuffer() {
+        if (p) {
+            cudaStreamSynchronize(h->stream);
+            h->release(p, bytes);
+        }
+    }
+};
+
+constexpr size_t kListChunk = size_t(1) << 20;   // cells per probe / scatter launch
+
+lbm_status check_cell_list(lbm_handle* h, int64_t count, const int64_t* cells) {
+    if (count < 0) return h->fail(LBM_ERR_ARG, "negative cell count");
+    if (count > 0 && !cells) return h->fail(LBM_ERR_ARG, "cells is NULL");
+    for (int64_t k = 0; k < count; ++k)
+        if (cells[k] < 0 || cells[k] >= (int64_t)h->N)
+            return h->fail(LBM_ERR_ARG, "cell index " + std::to_string(cells[k]) + " at position " + std::to_string(k) +
+                                            " is outside [0, " + std::to_string(h->N) + ")");
+    return LBM_OK;
+}
 
 // reads the device status word (call after a stream synchronisation)
 lbm_status check_status(lbm_handle* h) {
@@ -199,6 +227,26 @@ extern "C" lbm_status lbm_set_block(lbm_handle* h, int bx, int by) {
     return LBM_OK;
 }
 
+namespace {
+
+__global__ void k_fill(float* p, size_t n, float v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+// node_u / node_rho of m listed cells (indices checked on the host, no
+// duplicates); u: 3 x m component-major or NULL, rho: m or NULL
+__global__ void k_scatter_nodes(const int64_t* cells, uint32_t m, const float* u, const float* rho, float* node_u,
+                                float* node_rho, size_t N, int comps) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+        const size_t n = (size_t)cells[k];
+        if (u)
+            for (int d = 0; d < 3; ++d) node_u[d * N + n] = d < comps ? u[(size_t)d * m + k] : 0.0f;
+        if (rho) node_rho[n] = rho[k];
+    }
+}
+
+}  // namespace
+
 extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* node_u, const float* node_rho) {
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
@@ -257,10 +305,8 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
             if (h->cuda(cudaMemcpyAsync(h->node_rho, node_rho, N * sizeof(float), cudaMemcpyHostToDevice, h->stream),
                         "node_rho upload")) return LBM_ERR_CUDA;
         } else {
-            std::vector<float> ones(N, 1.0f);
-            if (h->cuda(cudaMemcpyAsync(h->node_rho, ones.data(), N * sizeof(float), cudaMemcpyHostToDevice, h->stream),
-                        "node_rho upload")) return LBM_ERR_CUDA;
-            if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
+            k_fill<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, h->stream>>>(h->node_rho, N, 1.0f);
+            if (h->cuda(cudaGetLastError(), "fill kernel")) return LBM_ERR_CUDA;
         }
     }
     {
@@ -275,6 +321,59 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
     st2 = zero_solid(h);                 // solid cells hold no populations
     if (st2 != LBM_OK) return st2;
     if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_nodes(lbm_handle* h, int64_t count, const int64_t* cells, const float* node_u,
+                                    const float* node_rho) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    if (!h->flags) return h->fail(LBM_ERR_ARG, "lbm_set_nodes needs flags (call lbm_set_geometry first)");
+    if ((st = check_cell_list(h, count, cells)) != LBM_OK) return st;
+    {
+        std::vector<int64_t> sorted(cells, cells + count);
+        std::sort(sorted.begin(), sorted.end());
+        auto dup = std::adjacent_find(sorted.begin(), sorted.end());
+        if (dup != sorted.end()) return h->fail(LBM_ERR_ARG, "cell " + std::to_string(*dup) + " is listed twice");
+    }
+    if (count == 0 || (!node_u && !node_rho)) return LBM_OK;
+    const size_t N = h->N;
+    if (node_u && !h->node_u) {
+        h->node_u = (float*)h->alloc(3 * N * sizeof(float));
+        if (!h->node_u) return h->fail(LBM_ERR_OOM, "node_u");
+        if (h->cuda(cudaMemsetAsync(h->node_u, 0, 3 * N * sizeof(float), h->stream), "memset")) return LBM_ERR_CUDA;
+    }
+    if (node_rho && !h->node_rho) {
+        h->node_rho = (float*)h->alloc(N * sizeof(float));
+        if (!h->node_rho) return h->fail(LBM_ERR_OOM, "node_rho");
+        k_fill<<<(unsigned)std::min<size_t>((N + 255) / 256, 152 * 16), 256, 0, h->stream>>>(h->node_rho, N, 1.0f);
+        if (h->cuda(cudaGetLastError(), "fill kernel")) return LBM_ERR_CUDA;
+    }
+    const int comps = h->p.velset == LBM_D2Q9 ? 2 : 3;   // D2Q9 ignores z
+    const size_t m_max = std::min<size_t>(kListChunk, (size_t)count);
+    TempBuffer buf(h, m_max * (sizeof(int64_t) + 4 * sizeof(float)));
+    if (!buf.p) return h->fail(LBM_ERR_OOM, "node staging buffer");
+    int64_t* dc = static_cast<int64_t*>(buf.p);
+    float* du = reinterpret_cast<float*>(dc + m_max);
+    float* dr = du + 3 * m_max;
+    for (int64_t k0 = 0; k0 < count; k0 += (int64_t)m_max) {
+        const size_t m = std::min<size_t>(m_max, (size_t)(count - k0));
+        if (h->cuda(cudaMemcpyAsync(dc, cells + k0, m * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream), "upload"))
+            return LBM_ERR_CUDA;
+        if (node_u)
+            for (int d = 0; d < comps; ++d)
+                if (h->cuda(cudaMemcpyAsync(du + d * m, node_u + (size_t)d * count + k0, m * sizeof(float),
+                                            cudaMemcpyHostToDevice, h->stream), "upload"))
+                    return LBM_ERR_CUDA;
+        if (node_rho && h->cuda(cudaMemcpyAsync(dr, node_rho + k0, m * sizeof(float), cudaMemcpyHostToDevice, h->stream),
+                                "upload"))
+            return LBM_ERR_CUDA;
+        k_scatter_nodes<<<(unsigned)((m + 255) / 256), 256, 0, h->stream>>>(dc, (uint32_t)m, node_u ? du : nullptr,
+                                                                           node_rho ? dr : nullptr, h->node_u,
+                                                                           h->node_rho, N, comps);
+        if (h->cuda(cudaGetLastError(), "scatter kernel")) return LBM_ERR_CUDA;
+        if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;   // staging is reused
+    }
     return LBM_OK;
 }
 
@@ -551,6 +650,78 @@ extern "C" lbm_status lbm_get_f(lbm_handle* h, double* f) {
     };
     st = h->fp64() ? probe_chunks(h, h->kd, PROBE_F, h->q, download)
                    : probe_chunks(h, h->kf, PROBE_F, h->q, download);
+    return st == LBM_OK ? check_status(h) : st;
+}
+
+namespace {
+
+// Probe kernel over a list of cells, in chunks of at most kListChunk cells;
+// download(k0, m, out) copies m cells' results (per_cell x m doubles) out.
+template <class R>
+lbm_status probe_list(lbm_handle* h, const Relax<R>& k, int mode, int per_cell, int64_t count, const int64_t* cells,
+                      const std::function<lbm_status(int64_t, size_t, const double*)>& download) {
+    const size_t m_max = std::min<size_t>(kListChunk, (size_t)count);
+    TempBuffer buf(h, m_max * (per_cell + 1) * sizeof(double));
+    if (!buf.p) return h->fail(LBM_ERR_OOM, "probe buffer");
+    double* out = static_cast<double*>(buf.p);
+    int64_t* dev_cells = reinterpret_cast<int64_t*>(out + (size_t)per_cell * m_max);
+    for (int64_t k0 = 0; k0 < count; k0 += (int64_t)m_max) {
+        const size_t m = std::min<size_t>(m_max, (size_t)(count - k0));
+        if (h->cuda(cudaMemcpyAsync(dev_cells, cells + k0, m * sizeof(int64_t), cudaMemcpyHostToDevice, h->stream),
+                    "cell list upload")) return LBM_ERR_CUDA;
+        ProbeArgs<R> pa{};
+        pa.a = h->args(k, h->aa() ? 0 : h->cur);
+        pa.out = out;
+        pa.partial = h->partial;
+        pa.cells = dev_cells;
+        pa.ncells = (uint32_t)m;
+        Launch L;
+        L.block = dim3(256);
+        L.grid = dim3((unsigned)((m + 255) / 256));
+        L.stream = h->stream;
+        if (h->cuda(h->ks->probe[h->layout_now()](&pa, mode, L), "probe kernel")) return LBM_ERR_CUDA;
+        lbm_status st = download(k0, m, out);
+        if (st != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_get_f_cells(lbm_handle* h, int64_t count, const int64_t* cells, double* f) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    if (count > 0 && !f) return h->fail(LBM_ERR_ARG, "f is NULL");
+    if ((st = check_cell_list(h, count, cells)) != LBM_OK) return st;
+    if (count == 0) return LBM_OK;
+    auto download = [&](int64_t k0, size_t m, const double* out) -> lbm_status {
+        for (int i = 0; i < h->q; ++i)
+            if (h->cuda(cudaMemcpyAsync(f + (size_t)i * count + k0, out + (size_t)i * m, m * sizeof(double),
+                                        cudaMemcpyDeviceToHost, h->stream), "f download"))
+                return LBM_ERR_CUDA;
+        return h->cuda(cudaStreamSynchronize(h->stream), "sync");
+    };
+    st = h->fp64() ? probe_list(h, h->kd, PROBE_F, h->q, count, cells, download)
+                   : probe_list(h, h->kf, PROBE_F, h->q, count, cells, download);
+    return st == LBM_OK ? check_status(h) : st;
+}
+
+extern "C" lbm_status lbm_get_rho_u_cells(lbm_handle* h, int64_t count, const int64_t* cells, double* rho,
+                                          double* ux, double* uy, double* uz) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    if ((st = check_cell_list(h, count, cells)) != LBM_OK) return st;
+    if (count == 0) return LBM_OK;
+    double* dst[4] = {rho, ux, uy, uz};
+    auto download = [&](int64_t k0, size_t m, const double* out) -> lbm_status {
+        for (int c = 0; c < 4; ++c)
+            if (dst[c] && h->cuda(cudaMemcpyAsync(dst[c] + k0, out + (size_t)c * m, m * sizeof(double),
+                                                  cudaMemcpyDeviceToHost, h->stream), "fields download"))
+                return LBM_ERR_CUDA;
+        return h->cuda(cudaStreamSynchronize(h->stream), "sync");
+    };
+    st = h->fp64() ? probe_list(h, h->kd, PROBE_FIELDS, 4, count, cells, download)
+                   : probe_list(h, h->kf, PROBE_FIELDS, 4, count, cells, download);
     return st == LBM_OK ? check_status(h) : st;
 }
 

@@ -524,25 +524,29 @@ __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __res
 // ---------------------------------------------------------------- probes
 // Per-cell quantities from the streamed populations: fields (rho, u with the
 // Guo half-force), the populations themselves, or FP64 mass / energy sums.
+// The cells are the planes z0..z1-1, or the listed cell indices when `cells`
+// is set (every index already checked to lie in [0, N) by the host).
 template <class R> struct ProbeArgs {
     StepArgs<R> a;
     int z0, z1;               // z-range handled by this launch
     double* out;              // FIELDS: 4 x count doubles; F: q x count doubles
     double* partial;          // REDUCE: 2 doubles per block
+    const int64_t* cells;     // optional list of cell indices
+    uint32_t ncells;          // its length
 };
 
 template <class V, int FMT, class R, int LAYOUT>
 __global__ void __launch_bounds__(256) k_probe(const ProbeArgs<R> p, int mode) {
     const StepArgs<R>& a = p.a;
     const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
-    const uint32_t count = plane * (uint32_t)(p.z1 - p.z0);
+    const uint32_t count = p.cells ? p.ncells : plane * (uint32_t)(p.z1 - p.z0);
     double m_acc = 0.0, e_acc = 0.0;
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-        const int z = p.z0 + (int)(t / plane);
-        const uint32_t r = t - (uint32_t)(z - p.z0) * plane;
+        const uint32_t n = p.cells ? (uint32_t)p.cells[t] : (uint32_t)p.z0 * plane + t;
+        const int z = (int)(n / plane);
+        const uint32_t r = n - (uint32_t)z * plane;
         const int y = (int)(r / (uint32_t)a.nx);
         const int x = (int)(r - (uint32_t)y * a.nx);
-        const uint32_t n = (uint32_t)z * plane + r;
         const uint32_t fl = a.flags ? a.flags[n] : 0u;
         const bool solid = fl & F_WALL;
         R f[V::Q];

@@ -41,6 +41,7 @@ EXPORTS = [
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_step_each",
     "lbm_ensemble_set_block", "lbm_ensemble_autotune", "lbm_ensemble_destroy",
     "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant", "lbm_get_rho_u_static",
+    "lbm_set_nodes", "lbm_get_f_cells", "lbm_get_rho_u_cells",
 ]
 
 
@@ -103,6 +104,9 @@ def load() -> ctypes.CDLL:
             "lbm_get_rho_u": [P, P, P, P, P],
             "lbm_get_rho_u_static": [P, P, P, P, P],
             "lbm_get_f": [P, P],
+            "lbm_set_nodes": [P, I64, P, P, P],
+            "lbm_get_f_cells": [P, I64, P, P],
+            "lbm_get_rho_u_cells": [P, I64, P, P, P, P, P],
             "lbm_set_f": [P, P],
             "lbm_reduce": [P, pD, pD],
             "lbm_get_info": [P, ctypes.POINTER(lbm_info)],
@@ -254,6 +258,36 @@ class Lattice:
         nu = None if node_u is None else np.ascontiguousarray(node_u, dtype=np.float32).reshape(-1)
         nr = None if node_rho is None else np.ascontiguousarray(node_rho, dtype=np.float32).reshape(-1)
         self._c(self._L.lbm_set_geometry(self._h, _ptr(fl), _ptr(nu), _ptr(nr)))
+
+    def set_nodes(self, cells, node_u=None, node_rho=None):
+        """Boundary-node data of the listed cells only: node_u shaped (3, count),
+        node_rho (count,); either may be None (unchanged)."""
+        c = np.ascontiguousarray(cells, dtype=np.int64).reshape(-1)
+        nu = None if node_u is None else np.ascontiguousarray(node_u, dtype=np.float32).reshape(3, c.size)
+        nr = None if node_rho is None else np.ascontiguousarray(node_rho, dtype=np.float32).reshape(c.size)
+        self._c(self._L.lbm_set_nodes(self._h, c.size, _ptr(c), _ptr(nu), _ptr(nr)))
+
+    def _cells(self, cells):
+        c = np.asarray(cells, dtype=np.int64)
+        if c.ndim == 2 and c.shape[1] == 3:      # (z, y, x) triples
+            nz, ny, nx = self.shape
+            c = c[:, 2] + nx * (c[:, 1] + ny * c[:, 0])
+        return np.ascontiguousarray(c.reshape(-1))
+
+    def f_cells(self, cells):
+        """Streamed populations of listed cells (flat indices or (z, y, x)
+        triples), shaped (q, count)."""
+        c = self._cells(cells)
+        out = np.empty((self.q, c.size), dtype=np.float64)
+        self._c(self._L.lbm_get_f_cells(self._h, c.size, _ptr(c), _ptr(out)))
+        return out
+
+    def rho_u_cells(self, cells):
+        """(rho, ux, uy, uz) of listed cells, each shaped (count,)."""
+        c = self._cells(cells)
+        out = [np.empty(c.size, dtype=np.float64) for _ in range(4)]
+        self._c(self._L.lbm_get_rho_u_cells(self._h, c.size, _ptr(c), *[_ptr(a) for a in out]))
+        return tuple(out)
 
     def set_rho_u(self, rho=None, ux=None, uy=None, uz=None):
         arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)

@@ -65,6 +65,24 @@ def cavity(n, u_lid, ny=None, nz=None):
     return flags, node_u
 
 
+def cavity_flags(n):
+    """Flags of the n^3 lid-driven cavity of `cavity` alone (one byte per
+    cell), for lattices too large for full-size node arrays."""
+    flags = np.full((n, n, n), WALL, dtype=np.uint8)
+    flags[1:n - 1, 1:n - 1, 1:n - 1] = 0
+    flags[n - 1, :, :] = WALL | MOVING
+    return flags
+
+
+def cavity_lid(n, u_lid):
+    """The lid of the n^3 cavity as a sparse node list: (cell indices of the
+    z = n-1 plane, node velocities shaped (3, n*n) with u_y = u_lid)."""
+    cells = (n - 1) * n * n + np.arange(n * n, dtype=np.int64)
+    u = np.zeros((3, n * n), dtype=np.float32)
+    u[1] = u_lid
+    return cells, u
+
+
 def karman_channel(nx=1024, ny=256, nz=64, radius=24, cx=256, cy=128, u_in=0.05):
     """Channel along x: equilibrium inflow plane x = 0 (rho=1, u=(u_in,0,0)),
     zero-gradient outflow plane x = nx-1, free-slip walls at y = 0 and
