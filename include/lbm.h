@@ -241,6 +241,14 @@ int lbm_get_variant(const lbm_handle* h);
  * advance the lattice. */
 lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx, int* by);
 
+/* Self-test of the failure path (the paper has no counterpart): launches
+ * one kernel whose bounded wait, on an mbarrier that nothing arrives on,
+ * runs out after about a second, as a bulk copy that never lands would in
+ * the STAGED kernel.  Returns LBM_ERR_TIMEOUT; the handle is then poisoned
+ * exactly as after a real timeout (later calls give LBM_ERR_STATE) while the
+ * CUDA context stays usable for other handles.  No fault, trap or hang. */
+lbm_status lbm_selftest_wait_timeout(lbm_handle* h);
+
 const char* lbm_last_error(const lbm_handle* h);
 const char* lbm_status_string(lbm_status s);
 

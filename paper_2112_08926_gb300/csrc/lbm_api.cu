@@ -775,6 +775,31 @@ extern "C" lbm_status lbm_reduce(lbm_handle* h, double* mass, double* kinetic_en
     return h->fp64() ? reduce_impl(h, h->kd, mass, kinetic_energy) : reduce_impl(h, h->kf, mass, kinetic_energy);
 }
 
+namespace {
+
+// One thread waits on an mbarrier that nothing ever arrives on, with the same
+// bounded wait as the bulk-copy kernels; when it runs out, the thread reports
+// it through the handle's status word.
+__global__ void k_wait_unarrived(int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        lbm::mbar_init(&bar, 1);
+        lbm::mbar_fence_init();
+        if (!lbm::mbar_wait(&bar, 0)) atomicExch(status, 1);
+    }
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_selftest_wait_timeout(lbm_handle* h) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    k_wait_unarrived<<<1, 32, 0, h->stream>>>(h->status);
+    if (h->cuda(cudaGetLastError(), "wait kernel")) return LBM_ERR_CUDA;
+    if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
+    return check_status(h);
+}
+
 extern "C" lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info) {
     if (!h || !info) return LBM_ERR_ARG;
     info->q = h->q;

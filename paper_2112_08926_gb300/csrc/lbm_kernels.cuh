@@ -171,19 +171,21 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     const uint32_t n = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
-    uint32_t fl = 0;
-    if (FLAGS) {
-        fl = a.flags[n];
-        if (fl & F_WALL) return;
-    }
+    constexpr int LAYOUT = SCHEME == SCHEME_AB ? LAYOUT_AB
+                         : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
+    const uint32_t fl = FLAGS ? (uint32_t)a.flags[n] : 0u;
+    // The plain pull is issued for every cell together with the flag load,
+    // so the two memory latencies overlap; solid and equilibrium cells drop
+    // it, cells next to solid cells gather again with their boundaries.
     R f[V::Q];
+    gather<V, FMT, R, false, LAYOUT, IX>(a, src, x, y, z, n, 0u, f);
+    if (FLAGS && (fl & F_WALL)) return;
     if (FLAGS && (fl & F_EQ)) {
         const R u[3] = {(R)a.node_u[n], (R)a.node_u[(size_t)a.N + n], (R)a.node_u[2 * (size_t)a.N + n]};
         equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f);
     } else {
-        constexpr int LAYOUT = SCHEME == SCHEME_AB ? LAYOUT_AB
-                             : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
-        gather<V, FMT, R, FLAGS, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
+        if (FLAGS && (fl & (LAYOUT == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
+            gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
         collide<V, COLL, R, S::SL>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
@@ -228,7 +230,8 @@ __global__ void __launch_bounds__(256) k_step(const StepArgs<R> a) {
 // so the bytes in flight do not depend on registers.  Each population load
 // is then one shared-memory read at a constant offset (x-wrap by selecting
 // x-1, x or x+1); the per-cell arithmetic is cell_step's.  Every wait is
-// bounded: on timeout the kernel writes *status = 1 and returns.
+// bounded: on timeout the CTA writes *status = 1, waits (bounded) for the
+// copies it still has in flight and returns.
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
@@ -245,15 +248,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+    // suspends for at most ~2 us per poll (time-limit hint in ns)
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
                  " selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity), "r"(2000u) : "memory");
     return ok != 0;
 }
-// bounded wait: about a second of polling before giving up
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// bounded wait: gives up after about a second (global timer), or after 2^24
+// polls should the timer not advance
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    for (uint32_t k = 0; k < (1u << 22); ++k)
+    const uint64_t t0 = global_ns();
+    for (uint32_t k = 0; k < (1u << 24); ++k) {
         if (mbar_try_wait(bar, parity)) return true;
+        if ((k & 63) == 63 && global_ns() - t0 > kWaitLimitNs) return false;
+    }
     return false;
 }
 
@@ -316,8 +330,12 @@ __global__ void __launch_bounds__(512, 2) k_step_staged(const StepArgs<float> a,
     T* dst = (T*)a.dst;
     for (int k = 0; k < my; ++k) {
         const int st = k % STAGES;
-        if (!mbar_wait(&bars[st], (uint32_t)((k / STAGES) & 1))) {
-            if (lane == 0) atomicExch(status, 1);
+        const bool ok = mbar_wait(&bars[st], (uint32_t)((k / STAGES) & 1));
+        if (__syncthreads_or(!ok)) {   // CTA-uniform: flag, let the copies in flight land, leave
+            if (tid == 0) {
+                atomicExch(status, 1);
+                for (int q = k; q < my && q < k + STAGES; ++q) mbar_wait(&bars[q % STAGES], (uint32_t)((q / STAGES) & 1));
+            }
             return;
         }
         const int t = (int)blockIdx.x + k * (int)gridDim.x;

@@ -41,7 +41,7 @@ EXPORTS = [
     "lbm_ensemble_create", "lbm_ensemble_step", "lbm_ensemble_step_each",
     "lbm_ensemble_set_block", "lbm_ensemble_autotune", "lbm_ensemble_destroy",
     "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant", "lbm_get_rho_u_static",
-    "lbm_set_nodes", "lbm_get_f_cells", "lbm_get_rho_u_cells",
+    "lbm_set_nodes", "lbm_get_f_cells", "lbm_get_rho_u_cells", "lbm_selftest_wait_timeout",
 ]
 
 
@@ -105,6 +105,7 @@ def load() -> ctypes.CDLL:
             "lbm_get_rho_u_static": [P, P, P, P, P],
             "lbm_get_f": [P, P],
             "lbm_set_nodes": [P, I64, P, P, P],
+            "lbm_selftest_wait_timeout": [P],
             "lbm_get_f_cells": [P, I64, P, P],
             "lbm_get_rho_u_cells": [P, I64, P, P, P, P, P],
             "lbm_set_f": [P, P],
