@@ -261,6 +261,55 @@ def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0,
     return rows
 
 
+def strouhal(t, uy, d, u):
+    """St = f D / U from the mean spacing of upward zero crossings of u_y."""
+    t, uy = np.asarray(t, dtype=np.float64), np.asarray(uy, dtype=np.float64)
+    up = np.flatnonzero((uy[:-1] < 0) & (uy[1:] >= 0))
+    if up.size < 2:
+        return None
+    tc = t[up] - uy[up] * (t[up + 1] - t[up]) / (uy[up + 1] - uy[up])   # linear interpolation
+    return d / u / float(np.mean(np.diff(tc)))
+
+
+def karman(P, torch, steps=50000, t0=20000, every=20, tiers=(("FP64", "FP64"), ("FP32", "FP32"), ("FP32", "FP16C"))):
+    """D3Q19 SRT Karman vortex street, channel 1024 x 256 x 64 (Sec. 4.3 in a
+    3-D channel): cylinder of radius 24 along z at x = 256, equilibrium
+    inflow u = 0.05 at x = 0, zero-gradient outflow, free-slip side walls,
+    Re = U D / nu = 250, no body force.  Per tier: Strouhal number from u_y
+    probed at (352, 128, 32) over steps t0..steps, and the relative L2 of the
+    final velocity field against the FP64 tier."""
+    import workloads as W
+    nx, ny, nz, r, u_in, re = 1024, 256, 64, 24, 0.05, 250.0
+    tau = 0.5 + 3.0 * u_in * 2 * r / re
+    flags, node_u, node_rho = W.karman_channel(nx, ny, nz, radius=r, cx=256, cy=128, u_in=u_in)
+    fields = W.karman_initial_fields(nx, ny, nz, u_in=u_in)
+    probe = np.array([352 + nx * (128 + ny * 32)], dtype=np.int64)
+    out, ref = {}, None
+    for arith, storage in tiers:
+        g = P.Lattice(nx, ny, nz, "D3Q19", "SRT", storage, arith, "AB", tau=tau)
+        g.set_geometry(flags, node_u, node_rho)
+        g.set_rho_u(*fields)
+        g.step(t0)
+        ts, uys = [], []
+        t_start = time.perf_counter()
+        for t in range(t0, steps, every):
+            uys.append(float(g.rho_u_cells(probe)[2][0]))
+            ts.append(t)
+            g.step(every)
+        torch.cuda.synchronize()
+        _, ux, uy, uz = g.rho_u()
+        g.close()
+        u = np.stack([ux, uy, uz])
+        if ref is None:
+            ref = u
+        out[f"{arith}/{storage}"] = {
+            "strouhal": strouhal(ts, uys, 2 * r, u_in), "l2_u_vs_fp64": float(np.linalg.norm(u - ref) / np.linalg.norm(ref)),
+            "uy_probe_rms": float(np.sqrt(np.mean(np.square(uys)))), "tau": tau, "steps": steps,
+            "seconds_sampled_part": time.perf_counter() - t_start}
+        print(json.dumps({f"{arith}/{storage}": out[f"{arith}/{storage}"]}), file=sys.stderr, flush=True)
+    return out
+
+
 def bench_reference(args, rank, world):
     if rank != 0:
         return
@@ -304,6 +353,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cavity-sweep", action="store_true",
                     help="only the D3Q19 TRT lid-driven cavity size sweep (one JSON line)")
+    ap.add_argument("--karman", action="store_true",
+                    help="only the Karman vortex street accuracy run (Strouhal number, L2 vs FP64)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -321,6 +372,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2112_08926_gb300 as P
+
+    if args.karman:
+        if rank == 0:
+            print(json.dumps({"karman": karman(P, torch)}), flush=True)
+        return
 
     if args.cavity_sweep:
         if rank == 0:

@@ -89,9 +89,10 @@ __device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t
 // cell beside it, or bounce-back if that cell is solid too.  Addresses are
 // chosen with selects and all loads are issued before the moving-wall terms
 // are added, so the loads stay in flight together.
+// Returns the mask of directions whose upstream cell is solid (bit i).
 template <class V, int FMT, class R, bool AA, class IX>
-__device__ __forceinline__ void gather_boundary(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
-                                                const Nbr& nb, R* f) {
+__device__ __forceinline__ uint32_t gather_boundary(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
+                                                    const Nbr& nb, R* f) {
     using S = Storage<FMT>;
     const IX N = (IX)a.N;
     const uint32_t self = nb.self();
@@ -109,25 +110,30 @@ __device__ __forceinline__ void gather_boundary(const StepArgs<R>& a, const type
             constexpr int m0 = mirror<V>(i, 0), m1 = mirror<V>(i, 1), m2 = mirror<V>(i, 2);
             const uint32_t axis = (fy[i] >> 5) & 3u;
             const bool fs = wall && (fy[i] & F_FREESLIP) && axis < 3u;
-            const uint32_t j2 = nb.xo[axis == 0 ? 1 : 1 - cx] + nb.yo[axis == 1 ? 1 : 1 - cy] +
-                                nb.zo[axis == 2 ? 1 : 1 - cz];
+            // compile-time array indices only (a runtime index would put nb in local memory)
+            const uint32_t j2 = (axis == 0 ? nb.xo[1] : nb.xo[1 - cx]) + (axis == 1 ? nb.yo[1] : nb.yo[1 - cy]) +
+                                (axis == 2 ? nb.zo[1] : nb.zo[1 - cz]);
             const uint32_t f2 = fs ? (uint32_t)a.flags[j2] : F_WALL;
             if (!(f2 & F_WALL)) addr = (IX)(axis == 0 ? m0 : (axis == 1 ? m1 : m2)) * N + j2;
         }
         f[i] = S::template load_g<R>(src, addr);
     });
+    uint32_t walls = 0;
     static_for<0, V::Q>([&](auto I) {
         constexpr int i = I.value;
         if (fy[i] & F_MOVING) f[i] = f[i] + moving_term<V, i, R, S::SL>(a.node_u, a.N, nb.up<V, i>());
+        walls |= (fy[i] & F_WALL) ? (1u << i) : 0u;
     });
+    return walls;
 }
 
 // Streamed populations of cell n at (x,y,z) for the given memory layout.
 // Cells without solid neighbours (internal bit F_NEAR_SOLID clear) take the
 // plain pull, as in the flag-free kernel.
+// Returns the solid-upstream mask of gather_boundary (0 on the other paths).
 template <class V, int FMT, class R, bool FLAGS, int LAYOUT, class IX = size_t>
-__device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
-                                       int x, int y, int z, uint32_t n, uint32_t fl, R* f) {
+__device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
+                                           int x, int y, int z, uint32_t n, uint32_t fl, R* f) {
     using S = Storage<FMT>;
     if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {
         static_for<0, V::Q>([&](auto I) {
@@ -151,7 +157,7 @@ __device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Stor
             int sx = x;
             if (!AA && (fl & F_OUTFLOW)) sx = x == 0 ? a.nx - 1 : x - 1;
             const Nbr nb(sx, y, z, a.nx, a.ny, a.nz);
-            gather_boundary<V, FMT, R, AA, IX>(a, src, nb, f);
+            return gather_boundary<V, FMT, R, AA, IX>(a, src, nb, f);
         } else {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
             static_for<0, V::Q>([&](auto I) {
@@ -160,6 +166,7 @@ __device__ __forceinline__ void gather(const StepArgs<R>& a, const typename Stor
             });
         }
     }
+    return 0u;
 }
 
 // One fused stream-collide update of cell (x, y, z).
@@ -178,6 +185,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     // so the two memory latencies overlap; solid and equilibrium cells drop
     // it, cells next to solid cells gather again with their boundaries.
     R f[V::Q];
+    uint32_t walls = 0;   // directions with a solid upstream (= downstream of the opposite) cell
     gather<V, FMT, R, false, LAYOUT, IX>(a, src, x, y, z, n, 0u, f);
     if (FLAGS && (fl & F_WALL)) return;
     if (FLAGS && (fl & F_EQ)) {
@@ -185,7 +193,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
         equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f);
     } else {
         if (FLAGS && (fl & (LAYOUT == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
-            gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
+            walls = gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
         collide<V, COLL, R, S::SL>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
@@ -200,7 +208,8 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
             static_for<0, V::Q>([&](auto I) {
                 constexpr int i = I.value;
                 const uint32_t d = nb.down<V, i>();
-                const bool wall = a.flags[d] & F_WALL;   // reflected back into this cell
+                // the downstream cell of i is the upstream cell of opposite(i)
+                const bool wall = (walls >> opposite(i)) & 1u;   // reflected back into this cell
                 S::template store_g<R>(dst, wall ? (IX)opposite(i) * N + n : (IX)i * N + d, f[i]);
             });
         } else {
@@ -213,7 +222,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
 
 // IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic)
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
-__global__ void __launch_bounds__(256) k_step(const StepArgs<R> a) {
+__global__ void __launch_bounds__(256, 3) k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;

@@ -72,3 +72,56 @@ def test_member_stepped_outside_is_detected():
     with pytest.raises(P.LBMError) as ei:
         e.step(1)
     assert ei.value.status == 7
+
+
+def _full_ensemble(P, specs, storage, arith):
+    mem = []
+    for s in specs:
+        g = P.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", storage, arith, "AB", tau=s.tau)
+        g.set_geometry(W.cavity_flags(s.n))
+        g.set_nodes(*W.cavity_lid(s.n, s.u_lid))
+        g.set_rho_u()
+        mem.append(g)
+    return mem, P.Ensemble(mem)
+
+
+def test_full_ensemble_error_against_fp64():
+    """The 512-cavity workload (edges 16..128, splitmix64 seed 20211216):
+    FP16S members advanced by the batched launch against the same members in
+    FP64, 500 steps; every member's velocity error at 2048 sampled cells is
+    stated, and 16 seeded members equal the CPU oracle bit for bit."""
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=512, seed=20211216)
+    steps = 500
+    lo, elo = _full_ensemble(P, specs, "FP16S", "FP32")
+    hi, ehi = _full_ensemble(P, specs, "FP64", "FP64")
+    elo.autotune(trial_steps=2)            # trial steps are real steps: match them on the FP64 side
+    done = lo[0].info().step
+    ehi.step(done)
+    elo.step(steps - done)
+    ehi.step(steps - done)
+    rng = np.random.default_rng(5)
+    errs = []
+    for s, a, b in zip(specs, lo, hi):
+        cells = rng.integers(0, s.n ** 3, 2048)
+        ua = np.stack(a.rho_u_cells(cells)[1:])
+        ub = np.stack(b.rho_u_cells(cells)[1:])
+        errs.append(np.linalg.norm(ua - ub) / max(np.linalg.norm(ub), 1e-300))
+    errs = np.array(errs)
+    print(f"\n512 cavities, FP32/FP16S vs FP64/FP64 after {steps} steps: relative L2 of u at sampled cells: "
+          f"median {np.median(errs):.3e}, 90th percentile {np.percentile(errs, 90):.3e}, max {errs.max():.3e}")
+    assert np.median(errs) < 2e-2 and errs.max() < 1e-1
+    # 16 seeded members (the smallest edges) against the oracle, bit for bit
+    order = np.argsort([s.n for s in specs], kind="stable")[:16]
+    for k in order:
+        s = specs[k]
+        o = oracle.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", "ORD32", "FP16S", tau=s.tau)
+        flags, node_u = W.cavity(s.n, s.u_lid)
+        o.set_geometry(flags, node_u)
+        o.set_rho_u()
+        o.step(steps)
+        assert np.array_equal(lo[k].f(), o.f()), (k, s)
+    elo.close()
+    ehi.close()
+    for g in lo + hi:
+        g.close()
