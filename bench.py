@@ -229,7 +229,7 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
             "speedup": t_e / t_b, "launches_per_step": {"batched": 1, "per_launch": count}}
 
 
-def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1):
+def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1, only=None):
     """D3Q19 TRT lid-driven cavities N^3 (wall shell included, lid z = N-1
     moving along +y, rho = 1, u = 0 at start, tau from Re = u_lid (N-2) / nu):
     FP32 storage up to 512^3, 16-bit up to 1024^3 (A-B below 768^3, in-place
@@ -240,6 +240,8 @@ def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0,
     for storage in formats:
         sizes = [64, 96, 128, 192, 256, 384, 512] + ([] if storage in ("FP32", "FP64") else [768, 1024])
         for n in sizes:
+            if only and n not in only:
+                continue
             scheme = "AA" if n >= 768 else "AB"
             tau = 0.5 + 3.0 * u_lid * (n - 2) / re
             g = P.Lattice(n, n, n, "D3Q19", "TRT", storage, "FP32", scheme, tau=tau)
@@ -353,6 +355,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cavity-sweep", action="store_true",
                     help="only the D3Q19 TRT lid-driven cavity size sweep (one JSON line)")
+    ap.add_argument("--cavity-sizes", default="", help="comma-separated subset of the sweep's edge lengths")
     ap.add_argument("--karman", action="store_true",
                     help="only the Karman vortex street accuracy run (Strouhal number, L2 vs FP64)")
     args = ap.parse_args()
@@ -380,7 +383,8 @@ def main():
 
     if args.cavity_sweep:
         if rank == 0:
-            rows = cavity_sweep(P, torch, args.steps)
+            only = [int(v) for v in args.cavity_sizes.split(",")] if args.cavity_sizes else None
+            rows = cavity_sweep(P, torch, args.steps, only=only)
             print(json.dumps({"cavity_sweep": rows, "peak_gbs": peaks()[0]}), flush=True)
         return
 

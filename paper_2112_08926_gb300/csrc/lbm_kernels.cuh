@@ -74,6 +74,17 @@ struct Nbr {
     __device__ __forceinline__ uint32_t self() const { return xo[1] + yo[1] + zo[1]; }
 };
 
+// Address of element j of population slot `slot` in a population-major
+// copy.  With 32-bit indices (q N < 2^32) the element offset is one 32-bit
+// multiply-add; otherwise the slot's start (a product of kernel arguments
+// only, kept in uniform registers) is added to the 32-bit cell index, so
+// 64-bit lattices pay no 64-bit index arithmetic per thread.
+template <class IX, class T>
+__device__ __forceinline__ T* elem_ptr(T* p, int slot, uint32_t N, uint32_t j) {
+    if constexpr (sizeof(IX) == 4) return p + ((uint32_t)slot * N + j);
+    else return (p + (size_t)slot * (size_t)N) + j;
+}
+
 // Moving-wall term of the bounce-back (Sec. 4.4): 6 w_i rho_w (c_i . u_w),
 // rho_w = 1, u_w read at the wall cell m.
 template <class V, int I, class R, int SL>
@@ -94,7 +105,7 @@ template <class V, int FMT, class R, bool AA, class IX>
 __device__ __forceinline__ uint32_t gather_boundary(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
                                                     const Nbr& nb, R* f) {
     using S = Storage<FMT>;
-    const IX N = (IX)a.N;
+    const uint32_t N = a.N;
     const uint32_t self = nb.self();
     uint32_t fy[V::Q];
     static_for<0, V::Q>([&](auto I) { fy[I.value] = a.flags[nb.up<V, I.value>()]; });
@@ -104,7 +115,8 @@ __device__ __forceinline__ uint32_t gather_boundary(const StepArgs<R>& a, const 
         constexpr int bslot = AA ? i : opposite(i);
         const uint32_t j = nb.up<V, i>();
         const bool wall = fy[i] & F_WALL;
-        IX addr = wall ? (IX)bslot * N + self : (IX)slot * N + j;
+        int sl = wall ? bslot : slot;          // source population and cell
+        uint32_t cell = wall ? self : j;
         if constexpr (!AA) {
             constexpr int cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
             constexpr int m0 = mirror<V>(i, 0), m1 = mirror<V>(i, 1), m2 = mirror<V>(i, 2);
@@ -114,9 +126,12 @@ __device__ __forceinline__ uint32_t gather_boundary(const StepArgs<R>& a, const 
             const uint32_t j2 = (axis == 0 ? nb.xo[1] : nb.xo[1 - cx]) + (axis == 1 ? nb.yo[1] : nb.yo[1 - cy]) +
                                 (axis == 2 ? nb.zo[1] : nb.zo[1 - cz]);
             const uint32_t f2 = fs ? (uint32_t)a.flags[j2] : F_WALL;
-            if (!(f2 & F_WALL)) addr = (IX)(axis == 0 ? m0 : (axis == 1 ? m1 : m2)) * N + j2;
+            if (!(f2 & F_WALL)) {
+                sl = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
+                cell = j2;
+            }
         }
-        f[i] = S::template load_g<R>(src, addr);
+        f[i] = S::template load_g<R>(elem_ptr<IX>(src, sl, N, cell), 0u);
     });
     uint32_t walls = 0;
     static_for<0, V::Q>([&](auto I) {
@@ -137,7 +152,7 @@ __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename 
     using S = Storage<FMT>;
     if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {
         static_for<0, V::Q>([&](auto I) {
-            f[I.value] = S::template load_g<R>(src, (IX)I.value * (IX)a.N + n);
+            f[I.value] = S::template load_g<R>(elem_ptr<IX>(src, I.value, a.N, n), 0u);
         });
         if (FLAGS && (fl & F_NEAR_MOVING)) {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
@@ -162,7 +177,7 @@ __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename 
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
             static_for<0, V::Q>([&](auto I) {
                 constexpr int slot = AA ? opposite(I.value) : I.value;
-                f[I.value] = S::template load_g<R>(src, (IX)slot * (IX)a.N + nb.up<V, I.value>());
+                f[I.value] = S::template load_g<R>(elem_ptr<IX>(src, slot, a.N, nb.up<V, I.value>()), 0u);
             });
         }
     }
@@ -174,7 +189,6 @@ template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
 __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, int z) {
     using S = Storage<FMT>;
     using T = typename S::T;
-    const IX N = (IX)a.N;
     const uint32_t n = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
@@ -197,10 +211,10 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
         collide<V, COLL, R, S::SL>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
-        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(dst, (IX)I.value * N + n, f[I.value]); });
+        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(elem_ptr<IX>(dst, I.value, a.N, n), 0u, f[I.value]); });
     } else if constexpr (SCHEME == SCHEME_AA_LOC) {
         static_for<0, V::Q>([&](auto I) {
-            S::template store_g<R>(dst, (IX)opposite(I.value) * N + n, f[I.value]);
+            S::template store_g<R>(elem_ptr<IX>(dst, opposite(I.value), a.N, n), 0u, f[I.value]);
         });
     } else {
         const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
@@ -210,11 +224,11 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
                 const uint32_t d = nb.down<V, i>();
                 // the downstream cell of i is the upstream cell of opposite(i)
                 const bool wall = (walls >> opposite(i)) & 1u;   // reflected back into this cell
-                S::template store_g<R>(dst, wall ? (IX)opposite(i) * N + n : (IX)i * N + d, f[i]);
+                S::template store_g<R>(elem_ptr<IX>(dst, wall ? opposite(i) : i, a.N, wall ? n : d), 0u, f[i]);
             });
         } else {
             static_for<0, V::Q>([&](auto I) {
-                S::template store_g<R>(dst, (IX)I.value * N + nb.down<V, I.value>(), f[I.value]);
+                S::template store_g<R>(elem_ptr<IX>(dst, I.value, a.N, nb.down<V, I.value>()), 0u, f[I.value]);
             });
         }
     }
@@ -222,7 +236,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
 
 // IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic)
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
-__global__ void __launch_bounds__(256, 3) k_step(const StepArgs<R> a) {
+__global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : 3) k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
