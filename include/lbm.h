@@ -81,6 +81,9 @@ typedef struct {
     double tau;         /* relaxation time (> 0.5); omega = 1/tau (appendix, SRT) */
     double trt_lambda;  /* TRT magic parameter (tau+ - 1/2)(tau- - 1/2), e.g. 3/16 */
     double force[3];    /* Guo body force per volume (Sec. 4.1); D2Q9 ignores z */
+    int no_ddf_shifting; /* 0 (default): populations stored shifted, f - w (Sec. 2.2);
+                            1: stored unshifted, the ablation of the paper's dashed
+                            curves (appendix, "without DDF-shifting") */
 } lbm_params;
 
 typedef struct {
@@ -94,7 +97,7 @@ typedef struct lbm_handle lbm_handle;
 
 /* Create a lattice.  Allocates the population copies (one for A-A, two for
  * A-B), flags and boundary-node arrays, and scratch.  All cells start as
- * fluid with zero populations (rho = 1, u = 0).  cuda_stream is a
+ * fluid at rest (rho = 1, u = 0: zero shifted populations).  cuda_stream is a
  * cudaStream_t; NULL selects the legacy default stream.
  * Errors: LBM_ERR_ARG (bad sizes/enums/tau), LBM_ERR_UNSUPPORTED (FP64
  * arithmetic with 16-bit storage, more than 2^31 cells), LBM_ERR_OOM,
@@ -112,7 +115,9 @@ lbm_status lbm_destroy(lbm_handle* h);
  * of EQ cells) or NULL (zero); node_rho: N floats (EQ density) or NULL (1).
  * The populations of cells that are solid in the new geometry are set to
  * zero.  With A-A streaming, OUTFLOW and FREESLIP cells give
- * LBM_ERR_UNSUPPORTED.  Invalid bit combinations give LBM_ERR_ARG. */
+ * LBM_ERR_UNSUPPORTED.  Invalid bit combinations, and OUTFLOW cells whose
+ * -x neighbour is solid (an outflow cell pulls as if it sat there), give
+ * LBM_ERR_ARG. */
 lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* node_u,
                             const float* node_rho);
 
@@ -129,8 +134,8 @@ lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* no
 lbm_status lbm_set_nodes(lbm_handle* h, int64_t count, const int64_t* cells, const float* node_u,
                          const float* node_rho);
 
-/* Initialise every non-solid cell with the shifted equilibrium (Sec. 2.2)
- * of the given density and velocity (host arrays of N doubles; NULL means
+/* Initialise every non-solid cell with the shifted equilibrium (Sec. 2.2;
+ * the plain one with no_ddf_shifting) of the given density and velocity (host arrays of N doubles; NULL means
  * rho = 1 / u = 0), converted to the arithmetic precision first; solid cells
  * get zero populations.  Resets the step counter to 0. */
 lbm_status lbm_set_rho_u(lbm_handle* h, const double* rho, const double* ux,
@@ -166,8 +171,8 @@ lbm_status lbm_get_rho_u(lbm_handle* h, double* rho, double* ux, double* uy, dou
  * synchronises the lattice's stream. */
 lbm_status lbm_get_rho_u_static(lbm_handle* h, double* rho, double* ux, double* uy, double* uz);
 
-/* Streamed populations f_i(x) (shifted, decoded, exactly as the next
- * collision reads them) into a host array of q*N doubles; solid cells 0. */
+/* Streamed populations f_i(x) (shifted unless no_ddf_shifting, decoded,
+ * exactly as the next collision reads them) into a host array of q*N doubles; solid cells 0. */
 lbm_status lbm_get_f(lbm_handle* h, double* f);
 
 /* Point probes: the streamed populations (as lbm_get_f) of `count` listed
@@ -272,10 +277,12 @@ typedef struct lbm_ensemble lbm_ensemble;
  * the ensemble adds a device descriptor table and a per-tile member table.
  * All launches go to the first member's stream. */
 lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out);
-/* Advance every member nsteps steps: one launch per step over all members,
- * replayed from a CUDA graph of up to 64 steps. */
+/* Advance every member nsteps steps: per step one launch over the plain
+ * cells of all members and one over the listed boundary cells of all
+ * members, replayed from a CUDA graph of up to 64 steps. */
 lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps);
-/* Same result, one launch per member per step (the baseline). */
+/* Same result, member by member (two launches per member per step: the
+ * baseline). */
 lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps);
 /* Cells per tile (thread block) of the ensemble launch: bx a multiple of 32
  * in [32, 256], by must be 1 (tiles are runs of consecutive cells). */

@@ -61,7 +61,7 @@ class _Params(ctypes.Structure):
         ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
         ("velset", ctypes.c_int), ("collision", ctypes.c_int), ("arith", ctypes.c_int),
         ("storage", ctypes.c_int), ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
-        ("force", ctypes.c_double * 3),
+        ("force", ctypes.c_double * 3), ("no_shift", ctypes.c_int),
     ]
 
 
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
             L.orc_create.argtypes = [ctypes.POINTER(_Params)]
             L.orc_destroy.argtypes = [P]
             L.orc_set_geometry.argtypes = [P, P, P, P]
+            L.orc_set_geometry.restype = ctypes.c_int
             L.orc_set_rho_u.argtypes = [P, P, P, P, P]
             L.orc_set_f.argtypes = [P, P]
             L.orc_step.argtypes = [P, i64]
@@ -149,10 +150,10 @@ class Lattice:
     """A-B pull lattice on the CPU; arrays are shaped (nz, ny, nx)."""
 
     def __init__(self, nx, ny, nz, velset="D3Q19", collision="SRT", arith="DEF64",
-                 storage="FP64", tau=0.8, trt_lambda=3.0 / 16.0, force=(0.0, 0.0, 0.0)):
+                 storage="FP64", tau=0.8, trt_lambda=3.0 / 16.0, force=(0.0, 0.0, 0.0), shifting=True):
         p = _Params(nx, ny, nz, VELSETS[velset], COLLISIONS[collision], ARITH[arith],
                     FORMATS[storage], float(tau), float(trt_lambda),
-                    (ctypes.c_double * 3)(*[float(v) for v in force]))
+                    (ctypes.c_double * 3)(*[float(v) for v in force]), 0 if shifting else 1)
         self._h = lib().orc_create(ctypes.byref(p))
         if not self._h:
             raise ValueError("oracle rejected the lattice parameters")
@@ -170,8 +171,9 @@ class Lattice:
         fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
         nu = None if node_u is None else np.ascontiguousarray(node_u, dtype=np.float32).reshape(-1)
         nr = None if node_rho is None else np.ascontiguousarray(node_rho, dtype=np.float32).reshape(-1)
-        lib().orc_set_geometry(self._h, None if fl is None else _ptr(fl),
-                               None if nu is None else _ptr(nu), None if nr is None else _ptr(nr))
+        if lib().orc_set_geometry(self._h, None if fl is None else _ptr(fl),
+                                  None if nu is None else _ptr(nu), None if nr is None else _ptr(nr)):
+            raise ValueError("an OUTFLOW cell's -x neighbour is solid")
 
     def set_rho_u(self, rho=None, ux=None, uy=None, uz=None):
         arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)

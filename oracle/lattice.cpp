@@ -128,6 +128,7 @@ struct Ordered {
     const VelSet& vs;
     R w[27], k6[27], w3[27];
     R om, c1, omp, omm, cSp, cSm, cs, F[3];
+    R sh;   /* 1: shifted populations, 0: unshifted */
     bool force;
 
     explicit Ordered(const orc_lattice* lat) : L(lat), vs(lat->vs) {
@@ -146,6 +147,7 @@ struct Ordered {
         cs = (R)(1.0 / std::sqrt(3.0));
         for (int a = 0; a < 3; ++a) F[a] = (R)L->p.force[a];
         force = L->has_force();
+        sh = L->p.no_shift ? (R)0 : (R)1;
     }
 
     /* sum_a c_a * v_a over the non-zero components, in axis order:
@@ -167,11 +169,12 @@ struct Ordered {
         return k6[i] * csum(vs.c[i], uw);
     }
 
-    /* rho (sum in index order, +1 last) and the alternating-sign momentum */
+    /* rho (sum in index order, +1 last; +0 for unshifted populations, the
+     * appendix's rho = sum f) and the alternating-sign momentum */
     void moments(const R* f, R& rho, R j[3]) const {
         rho = f[0];
         for (int i = 1; i < vs.q; ++i) rho = rho + f[i];
-        rho = rho + (R)1;
+        rho = rho + sh;
         for (int a = 0; a < 3; ++a) {
             R s = 0;
             bool first = true;
@@ -193,14 +196,16 @@ struct Ordered {
         for (int a = 0; a < 3; ++a) u[a] = (force ? fmaR((R)0.5, F[a], j[a]) : j[a]) * inv;
     }
 
-    /* three-FMA shifted equilibrium; returns B_p of every pair in Bp */
+    /* three-FMA shifted equilibrium; returns B_p of every pair in Bp.  For
+     * unshifted populations D = w rho (rho - 0): the same three FMAs then give
+     * w rho (1 + B + (B^2 + C) / 2), the appendix's plain equilibrium. */
     void equilibrium(R rho, const R u[3], R* feq, R* Bp) const {
         R t = u[0] * u[0];
         t = t + u[1] * u[1];
         if (vs.d == 3) t = t + u[2] * u[2];
         const R C = (R)(-3) * t;
         const R u3[3] = {(R)3 * u[0], (R)3 * u[1], (R)3 * u[2]};
-        const R rhom1 = rho - (R)1;
+        const R rhom1 = rho - sh;
         feq[0] = fmaR(w[0] * rho, (R)0.5 * C, w[0] * rhom1);
         for (int p = 1; p < vs.q; p += 2) {
             const R A = w[p] * rho, D = w[p] * rhom1;
@@ -292,7 +297,7 @@ struct Definition {
             s += f[i];
             for (int a = 0; a < 3; ++a) j[a] += vs.c[i][a] * f[i];
         }
-        rho = s + 1.0;
+        rho = L->p.no_shift ? s : s + 1.0;   /* Sec. 2.2 / appendix without shifting */
         for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * L->p.force[a]) / rho;
     }
 
@@ -300,7 +305,10 @@ struct Definition {
         const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
         for (int i = 0; i < vs.q; ++i) {
             const double cu = dot(vs.c[i], u);
-            feq[i] = vs.w[i] * rho * (4.5 * cu * cu - 1.5 * uu + 3.0 * cu) + vs.w[i] * (rho - 1.0);
+            if (L->p.no_shift)   /* appendix, equilibrium without DDF-shifting */
+                feq[i] = vs.w[i] * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            else                 /* Sec. 2.2, shifted equilibrium */
+                feq[i] = vs.w[i] * rho * (4.5 * cu * cu - 1.5 * uu + 3.0 * cu) + vs.w[i] * (rho - 1.0);
         }
     }
 
@@ -506,13 +514,23 @@ orc_lattice* orc_create(const orc_params* p) {
     L->nrho.assign(L->N, 1.0f);
     L->fa.assign(L->vs.q * L->N, 0.0);
     L->fb.assign(L->vs.q * L->N, 0.0);
+    if (p->no_shift) orc_set_rho_u(L, nullptr, nullptr, nullptr, nullptr);   /* rest is not zero */
     return L;
 }
 
 void orc_destroy(orc_lattice* L) { delete L; }
 
-void orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u, const float* node_rho) {
+int orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u, const float* node_rho) {
     const int64_t N = L->N;
+    /* an outflow cell pulls as if it sat one cell upstream in x; that cell
+     * must hold populations */
+    if (flags)
+        for (int64_t n = 0; n < N; ++n) {
+            if (!(flags[n] & ORC_OUTFLOW)) continue;
+            const int x = (int)(n % L->p.nx);
+            const int64_t m = n - x + (x == 0 ? L->p.nx - 1 : x - 1);
+            if (flags[m] & ORC_WALL) return 1;
+        }
     if (flags) std::memcpy(L->flags.data(), flags, N);
     else std::fill(L->flags.begin(), L->flags.end(), 0);
     if (node_u) std::memcpy(L->nu.data(), node_u, 3 * N * sizeof(float));
@@ -524,6 +542,7 @@ void orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u,
     for (int64_t n = 0; n < N; ++n)
         if (L->solid(n))
             for (int i = 0; i < L->vs.q; ++i) L->fa[i * N + n] = L->fb[i * N + n] = 0.0;
+    return 0;
 }
 
 void orc_set_rho_u(orc_lattice* L, const double* rho, const double* ux, const double* uy, const double* uz) {

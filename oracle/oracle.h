@@ -74,6 +74,8 @@ typedef struct {
     double tau;        /* relaxation time, omega = 1/tau */
     double trt_lambda; /* TRT magic parameter (only for ORC_TRT) */
     double force[3];   /* Guo body force per volume, lattice units */
+    int no_shift;      /* 0: populations stored shifted, f - w (Sec. 2.2);
+                          1: stored as f (appendix, LBM "without DDF-shifting") */
 } orc_params;
 
 typedef struct orc_lattice orc_lattice;
@@ -87,7 +89,8 @@ void orc_destroy(orc_lattice* L);
 /* flags (N bytes), node_u (3*N floats, component-major: ux[N], uy[N], uz[N]) and
  * node_rho (N floats) may be NULL (all fluid / zero velocity / unit density);
  * the populations of solid cells are set to zero */
-void orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u,
+/* returns 1 (and changes nothing) if an OUTFLOW cell's -x neighbour is solid */
+int orc_set_geometry(orc_lattice* L, const uint8_t* flags, const float* node_u,
                       const float* node_rho);
 /* initialise every non-solid cell with the shifted equilibrium of (rho, u) */
 void orc_set_rho_u(orc_lattice* L, const double* rho, const double* ux,

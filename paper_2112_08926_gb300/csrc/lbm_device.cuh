@@ -343,9 +343,13 @@ __device__ __forceinline__ float maxR(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double maxR(double a, double b) { return fmax(a, b); }
 
 // Relaxation constants in arithmetic precision (computed on the host).
+// sh is the DDF shift (Sec. 2.2): 1 when populations are stored as f - w,
+// 0 for the unshifted ablation (appendix, "without DDF-shifting"), where the
+// same formulas with rho = sum f and D = w rho give the plain equilibrium.
 template <class R> struct Relax {
     R om, c1, omp, omm, cSp, cSm, cs;
     R F[3];
+    R sh;
     int force;
 };
 
@@ -396,12 +400,13 @@ template <int SL> struct Pow2 {
 // added last (Sec. 2.2): rho = (sum f) + 1, the exact sum of the scaled
 // values times 2^-SL being fused into that last addition; the momentum j is
 // returned scaled (alternating-sign sums over opposite pairs, Sec. 2.2).
+// sh = 0 (unshifted populations) adds nothing.
 template <class V, class R, int SL>
-__device__ __forceinline__ void moments(const R* g, R& rho, R* j) {
+__device__ __forceinline__ void moments(const R* g, R& rho, R* j, R sh) {
     R s = g[0];
     static_for<1, V::Q>([&](auto I) { s = s + g[I.value]; });
-    if constexpr (SL == 0) rho = s + R(1);
-    else rho = fmaR(s, R(Pow2<SL>::down), R(1));
+    if constexpr (SL == 0) rho = s + sh;
+    else rho = fmaR(s, R(Pow2<SL>::down), sh);
     j[0] = jsum<V, 0, 1, true, R>(g, R(0));
     j[1] = jsum<V, 1, 1, true, R>(g, R(0));
     j[2] = jsum<V, 2, 1, true, R>(g, R(0));
@@ -428,15 +433,15 @@ __device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R
 // Shifted equilibrium with three FMAs per population (footnote of Sec. 2.2):
 // f^eq-s = A (0.5 (B^2 + C) +- B) + D, A = w rho, B = 3 u.c, C = -3 u.u, D = w (rho - 1),
 // returned times 2^SL (the weights carry the scale).  Bp receives B of the
-// first member of every pair.
+// first member of every pair.  With sh = 0, D = w rho: the unshifted f^eq.
 template <class V, class R, int SL>
-__device__ __forceinline__ void equilibrium(R rho, const R* u, R* feq, R* Bp) {
+__device__ __forceinline__ void equilibrium(R rho, const R* u, R* feq, R* Bp, R sh) {
     R t = u[0] * u[0];
     t = t + u[1] * u[1];
     if constexpr (V::D == 3) t = t + u[2] * u[2];
     const R C = R(-3) * t;
     const R u3[3] = {R(3) * u[0], R(3) * u[1], R(3) * u[2]};
-    const R rhom1 = rho - R(1);
+    const R rhom1 = rho - sh;
     const R w0 = R(V::w(0) * Pow2<SL>::up);
     feq[0] = fmaR(w0 * rho, R(0.5) * C, w0 * rhom1);
     static_for<0, (V::Q - 1) / 2>([&](auto K) {
@@ -471,12 +476,12 @@ __device__ __forceinline__ void guo_source(const Relax<R>& k, const R* u, const 
 template <class V, int COLL, class R, int SL>
 __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
     R rho, j[3], u[3];
-    moments<V, R, SL>(f, rho, j);
+    moments<V, R, SL>(f, rho, j, k.sh);
     velocity<R, SL>(k, rho, j, u);
 #pragma unroll
     for (int a = 0; a < 3; ++a) u[a] = minR(maxR(u[a], -k.cs), k.cs);
     R feq[V::Q], Bp[V::Q], S[V::Q];
-    equilibrium<V, R, SL>(rho, u, feq, Bp);
+    equilibrium<V, R, SL>(rho, u, feq, Bp, k.sh);
     if (k.force) guo_source<V, R, SL>(k, u, Bp, S);
     if constexpr (COLL == 0) {   // SRT: fma(1 - omega, f, omega f^eq)
         if (k.force) {
@@ -510,9 +515,9 @@ __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
 }
 
 template <class V, class R, int SL>
-__device__ __forceinline__ void equilibrium_only(R rho, const R* u, R* feq) {
+__device__ __forceinline__ void equilibrium_only(R rho, const R* u, R* feq, R sh) {
     R Bp[V::Q];
-    equilibrium<V, R, SL>(rho, u, feq, Bp);
+    equilibrium<V, R, SL>(rho, u, feq, Bp, sh);
 }
 
 }  // namespace lbm

@@ -27,9 +27,23 @@ cudaError_t launch_step(const void* args, const Launch& L) {
 }
 
 template <class V, int COLL, int SCHEME, class IX>
+cudaError_t launch_list(const void* args, const uint32_t* cells, uint32_t count, const Launch& L) {
+    k_step_list<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
+        *static_cast<const StepArgs<Real>*>(args), cells, count);
+    return cudaGetLastError();
+}
+
+template <class V, int COLL, int SCHEME, class IX>
 cudaError_t launch_ens(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
     k_ensemble_step<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
         static_cast<const EnsMember<Real>*>(members), tile_member, parity);
+    return cudaGetLastError();
+}
+
+template <class V, int COLL, int SCHEME, class IX>
+cudaError_t launch_ens_list(const void* members, const uint64_t* cells, uint32_t count, int parity, const Launch& L) {
+    k_ensemble_list<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
+        static_cast<const EnsMember<Real>*>(members), cells, count, parity);
     return cudaGetLastError();
 }
 
@@ -82,8 +96,12 @@ void fill() {
         s.step[SC.value][1][0] = launch_step<V, COLL, SC.value, true, size_t>;
         s.step[SC.value][0][1] = launch_step<V, COLL, SC.value, false, uint32_t>;
         s.step[SC.value][1][1] = launch_step<V, COLL, SC.value, true, uint32_t>;
+        s.list[SC.value][0] = launch_list<V, COLL, SC.value, size_t>;
+        s.list[SC.value][1] = launch_list<V, COLL, SC.value, uint32_t>;
         s.ens[SC.value][0] = launch_ens<V, COLL, SC.value, size_t>;
         s.ens[SC.value][1] = launch_ens<V, COLL, SC.value, uint32_t>;
+        s.ens_list[SC.value][0] = launch_ens_list<V, COLL, SC.value, size_t>;
+        s.ens_list[SC.value][1] = launch_ens_list<V, COLL, SC.value, uint32_t>;
     });
     s.probe[LAYOUT_AB] = launch_probe<V, LAYOUT_AB>;
     s.probe[LAYOUT_AA_SWAPPED] = launch_probe<V, LAYOUT_AA_SWAPPED>;

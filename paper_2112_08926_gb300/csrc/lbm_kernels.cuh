@@ -184,8 +184,11 @@ __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename 
     return 0u;
 }
 
-// One fused stream-collide update of cell (x, y, z).
-template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
+// One fused stream-collide update of cell (x, y, z).  PLAIN_ONLY (with
+// flags): only cells whose flag byte is 0 -- fluid, no solid, moving or
+// equilibrium neighbour -- are updated; the others are left to the list
+// kernel, so no warp runs the boundary path for a few of its lanes.
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX, bool PLAIN_ONLY = false>
 __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, int z) {
     using S = Storage<FMT>;
     using T = typename S::T;
@@ -201,10 +204,11 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     R f[V::Q];
     uint32_t walls = 0;   // directions with a solid upstream (= downstream of the opposite) cell
     gather<V, FMT, R, false, LAYOUT, IX>(a, src, x, y, z, n, 0u, f);
+    if (PLAIN_ONLY && fl != 0u) return;
     if (FLAGS && (fl & F_WALL)) return;
     if (FLAGS && (fl & F_EQ)) {
         const R u[3] = {(R)a.node_u[n], (R)a.node_u[(size_t)a.N + n], (R)a.node_u[2 * (size_t)a.N + n]};
-        equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f);
+        equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f, a.k.sh);
     } else {
         if (FLAGS && (fl & (LAYOUT == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
             walls = gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
@@ -234,13 +238,30 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     }
 }
 
-// IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic)
+// IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic).
+// FLAGS: the lattice has flags; then this kernel updates the plain cells
+// (flag byte 0) only and k_step_list the listed others.
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
 __global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : 3) k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    cell_step<V, COLL, FMT, R, SCHEME, FLAGS, IX>(a, x, y, (int)blockIdx.z);
+    cell_step<V, COLL, FMT, R, SCHEME, FLAGS, IX, FLAGS>(a, x, y, (int)blockIdx.z);
+}
+
+// The non-plain cells of a flagged lattice (solid cells excluded): boundary
+// neighbours, equilibrium and outflow cells, from a list built when the
+// geometry is set, one per thread.
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
+__global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : 3)
+    k_step_list(const StepArgs<R> a, const uint32_t* __restrict__ cells, uint32_t count) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint32_t n = cells[t];
+    const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
+    const uint32_t z = n / plane, r = n - z * plane;
+    const uint32_t y = r / (uint32_t)a.nx, x = r - y * (uint32_t)a.nx;
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- staged kernel
@@ -548,12 +569,32 @@ template <class R> struct EnsMember {
     FastDiv by_plane, by_nx;
 };
 
+// The plain cells (flag byte 0) of every member; the others come from the
+// ensemble's list (k_ensemble_list).
 template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
 __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
     const uint32_t n = (blockIdx.x - M.tile0) * blockDim.x + threadIdx.x;
     if (n >= M.ncells) return;
+    const StepArgs<R> a = M.args[parity];
+    const uint32_t z = M.by_plane.div(n);
+    const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
+    const uint32_t y = M.by_nx.div(r);
+    const uint32_t x = r - y * (uint32_t)a.nx;
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, true>(a, (int)x, (int)y, (int)z);
+}
+
+// The non-plain cells of all members: entry = member << 32 | cell.
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
+__global__ void __launch_bounds__(256) k_ensemble_list(const EnsMember<R>* __restrict__ members,
+                                                        const uint64_t* __restrict__ cells, uint32_t count,
+                                                        int parity) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint64_t e = cells[t];
+    const EnsMember<R>& M = members[(uint32_t)(e >> 32)];
+    const uint32_t n = (uint32_t)e;
     const StepArgs<R> a = M.args[parity];
     const uint32_t z = M.by_plane.div(n);
     const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
@@ -610,7 +651,7 @@ __global__ void __launch_bounds__(256) k_probe(const ProbeArgs<R> p, int mode) {
             for (int d = 0; d < 3; ++d) u[d] = (double)a.node_u[(size_t)d * a.N + n];
         } else {
             R rr, j[3], uu[3];
-            moments<V, R, SL>(f, rr, j);
+            moments<V, R, SL>(f, rr, j, a.k.sh);
             velocity<R, SL>(a.k, rr, j, uu);
             rho = (double)rr;
             for (int d = 0; d < 3; ++d) u[d] = (double)uu[d];
@@ -682,7 +723,7 @@ __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
             const R rho = p.in[0] ? (R)p.in[0][t] : R(1);
             const R u[3] = {p.in[1] ? (R)p.in[1][t] : R(0), p.in[2] ? (R)p.in[2][t] : R(0),
                             (V::D == 3 && p.in[3]) ? (R)p.in[3][t] : R(0)};
-            equilibrium_only<V, R, 0>(rho, u, f);
+            equilibrium_only<V, R, 0>(rho, u, f, a.k.sh);
         }
         static_for<0, V::Q>([&](auto I) {
             constexpr int slot = AA ? opposite(I.value) : I.value;

@@ -57,7 +57,7 @@ class lbm_params(ctypes.Structure):
         ("velset", ctypes.c_int), ("collision", ctypes.c_int), ("storage", ctypes.c_int),
         ("arith", ctypes.c_int), ("scheme", ctypes.c_int),
         ("tau", ctypes.c_double), ("trt_lambda", ctypes.c_double),
-        ("force", ctypes.c_double * 3),
+        ("force", ctypes.c_double * 3), ("no_ddf_shifting", ctypes.c_int),
     ]
 
 
@@ -222,11 +222,11 @@ class Lattice:
 
     def __init__(self, nx, ny, nz, velset="D3Q19", collision="SRT", storage="FP32",
                  arith="FP32", scheme="AB", tau=0.8, trt_lambda=3.0 / 16.0,
-                 force=(0.0, 0.0, 0.0), stream=None, allocator=None):
+                 force=(0.0, 0.0, 0.0), stream=None, allocator=None, shifting=True):
         self._L = load()
         self.params = lbm_params(nx, ny, nz, VELSETS[velset], COLLISIONS[collision], STORAGES[storage],
                                  ARITHS[arith], SCHEMES[scheme], float(tau), float(trt_lambda),
-                                 (ctypes.c_double * 3)(*[float(v) for v in force]))
+                                 (ctypes.c_double * 3)(*[float(v) for v in force]), 0 if shifting else 1)
         self.allocator = allocator if allocator is not None else torch_allocator()
         self.stream = current_stream_ptr() if stream is None else stream
         self._h = None

@@ -174,3 +174,36 @@ def test_taylor_green_2d_energy_plateau():
     assert plateaus["FP32/P16_0S"] > 1e2 * eps["P16_0S"] ** 2
     # Sec. 4.2: FP64 arithmetic with FP32 storage plateaus far below FP32 / FP32
     assert plateaus["FP64/FP32"] < 1e-2 * plateaus["FP32/FP32"]
+
+
+def _plateau(P, arith, storage, shifting, L=256, u0=0.25, tau=1.0):
+    g = P.Lattice(L, L, 1, "D2Q9", "SRT", storage, arith, "AB", tau=tau, shifting=shifting)
+    g.set_rho_u(*W.taylor_green_extruded(L, u0, nz=1))
+    _, e0 = g.reduce()
+    prev, ratio, steps = e0, 1.0, 0
+    for _ in range(250):
+        g.step(1000)
+        steps += 1000
+        _, e = g.reduce()
+        ratio = e / e0
+        if e > 0.9 * prev:
+            break
+        prev = e
+    g.close()
+    return ratio, steps
+
+
+def test_taylor_green_2d_plateau_without_shifting():
+    """Sec. 4.2 (dashed curves): without DDF shifting the energy plateaus
+    sit far higher for every format; FP32 storage included."""
+    P = _pkg()
+    lines, res = [], {}
+    for arith, storage in [("FP32", "FP32"), ("FP32", "FP16"), ("FP32", "FP16S"), ("FP32", "FP16C"),
+                           ("FP32", "P16_1S"), ("FP32", "P16_2C")]:
+        (ps, ss), (pu, su) = _plateau(P, arith, storage, True), _plateau(P, arith, storage, False)
+        res[storage] = (ps, pu)
+        lines.append(f"{arith}/{storage:7s} plateau E/E0 shifted {ps:.3e} ({ss} steps)   "
+                     f"unshifted {pu:.3e} ({su} steps)")
+    print("\nD2Q9 Taylor-Green L=256 u0=0.25 tau=1, with and without DDF shifting\n" + "\n".join(lines))
+    for storage, (ps, pu) in res.items():
+        assert pu > 10 * ps, storage

@@ -302,3 +302,59 @@ def test_chunked_lattice_takes_flags_later():
     g.step(3)
     o.step(3)
     assert np.array_equal(g.f(), o.f())
+
+
+# ---------------------------------------------------------------- no DDF shifting
+def _pair(vs, coll, storage, arith, oarith, scheme, shifting, steps, force, geo, fields):
+    nz, ny, nx = SHAPES[vs]
+    g = P().Lattice(nx, ny, nz, vs, coll, storage, arith, scheme, tau=0.66, trt_lambda=0.2, force=force,
+                    shifting=shifting)
+    g.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    g.step(steps)
+    gout = g.f(), g.rho_u()
+    g.close()
+    o = oracle.Lattice(nx, ny, nz, vs, coll, oarith, "FP64" if oarith == "DEF64" else storage, tau=0.66,
+                       trt_lambda=0.2, force=force, shifting=shifting)
+    o.set_geometry(*geo)
+    o.set_rho_u(*fields)
+    o.step(steps)
+    return gout, (o.f(), o.rho_u())
+
+
+@pytest.mark.parametrize("vs", ["D2Q9", "D3Q19", "D3Q27"])
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+@pytest.mark.parametrize("storage", ["FP32", "FP16", "FP16S", "FP16C", "P16_1S", "P16_2C"])
+def test_unshifted_fp32_arithmetic_bitwise(vs, scheme, storage):
+    """The no-shifting ablation (appendix, without DDF-shifting): stored f,
+    rho = sum f, plain equilibrium; bit for bit the ordered FP32 oracle."""
+    geo = geometry(vs, scheme, 41)
+    fields = W.random_fields(SHAPES[vs], 42)
+    (gf, gu), (of, ou) = _pair(vs, "TRT" if storage in ("FP16S", "P16_2C") else "SRT", storage, "FP32", "ORD32",
+                               scheme, False, 21 if scheme == "AA" else 20, FORCE[vs], geo, fields)
+    assert np.array_equal(gf, of)
+    for a, b in zip(gu, ou):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("vs", ["D3Q19", "D3Q27"])
+def test_unshifted_fp64_tier_matches_definition(vs):
+    geo = geometry(vs, "AB", 43)
+    fields = W.random_fields(SHAPES[vs], 44)
+    (gf, _), (of, _) = _pair(vs, "SRT", "FP64", "FP64", "DEF64", "AB", False, 30, FORCE[vs], geo, fields)
+    assert np.linalg.norm(gf - of) / np.linalg.norm(of) < 1e-12
+
+
+def test_unshifted_lattice_starts_at_rest_and_chunked_layout_applies():
+    g = P().Lattice(128, 6, 5, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=0.7, shifting=False)
+    r, ux, uy, uz = g.rho_u()
+    assert np.abs(r - 1).max() < 1e-3 and np.abs(ux).max() == 0
+    assert g.info().layout == 1          # flag-free 16-bit A-B: chunked paired kernel
+    fields = W.random_fields((5, 6, 128), 45)
+    g.set_rho_u(*fields)
+    g.step(9)
+    o = oracle.Lattice(128, 6, 5, "D3Q19", "SRT", "ORD32", "FP16S", tau=0.7, shifting=False)
+    o.set_rho_u(*fields)
+    o.step(9)
+    assert np.array_equal(g.f(), o.f())
+    g.close()

@@ -259,3 +259,89 @@ def test_sixteen_bit_storage_holds_codec_values(fmt):
     L.step(3)
     f = L.f().astype(np.float32).reshape(-1)
     assert np.array_equal(oracle.decode(fmt, oracle.encode(fmt, f)), f)
+
+
+# ---------------------------------------------------------------- no DDF shifting
+@pytest.mark.parametrize("vs,coll", [("D2Q9", "SRT"), ("D3Q19", "TRT"), ("D3Q27", "SRT")])
+def test_unshifted_lattice_is_shifted_lattice_plus_weights(vs, coll):
+    """Appendix, with and without DDF-shifting: the two formulations are the
+    same LBM, so in FP64 the unshifted populations equal the shifted ones plus
+    w_i (up to rounding), on every boundary kind, with forcing."""
+    shape = (1, 9, 11) if vs == "D2Q9" else (5, 6, 7)
+    flags, node_u, node_rho = W.random_geometry(shape, 31)
+    c, w = oracle.velset(vs)
+    res = {}
+    for shifting in (True, False):
+        L = oracle.Lattice(shape[2], shape[1], shape[0], vs, coll, "DEF64", "FP64", tau=0.7,
+                           force=(1e-5, -2e-5, 0 if vs == "D2Q9" else 1e-5), shifting=shifting)
+        L.set_geometry(flags, node_u, node_rho)
+        L.set_rho_u(*W.random_fields(shape, 32))
+        L.step(30)
+        res[shifting] = (L.f(), L.rho_u())
+    fs, fu = res[True][0], res[False][0]
+    fluid = (flags & W.WALL) == 0
+    diff = (fu - w.reshape(-1, 1, 1, 1) - fs)[:, fluid]
+    assert np.abs(diff).max() < 1e-13
+    for a, b in zip(res[True][1], res[False][1]):
+        assert np.abs(a - b).max() < 1e-13
+
+
+@pytest.mark.parametrize("vs", ["D2Q9", "D3Q19", "D3Q27"])
+def test_unshifted_equilibrium_moments(vs):
+    """Plain equilibrium (appendix, without shifting): sum f = rho, sum c f = rho u."""
+    c, w = oracle.velset(vs)
+    rng = np.random.default_rng(8)
+    for _ in range(5):
+        rho = 1 + 0.1 * rng.uniform(-1, 1)
+        u = 0.1 * rng.uniform(-1, 1, 3)
+        if vs == "D2Q9":
+            u[2] = 0.0
+        L = oracle.Lattice(1, 1, 1, vs, "SRT", "DEF64", "FP64", tau=0.8, shifting=False)
+        L.set_rho_u(np.array([rho]), np.array([u[0]]), np.array([u[1]]), np.array([u[2]]))
+        f = L.f().reshape(-1)
+        assert abs(f.sum() - rho) < 1e-14
+        assert np.abs(c.T @ f - rho * u).max() < 1e-14
+        r, ux, uy, uz = L.rho_u()
+        assert abs(r.item() - rho) < 1e-14
+
+
+def test_unshifted_lattice_starts_at_rest():
+    L = oracle.Lattice(3, 4, 5, "D3Q19", "SRT", "DEF64", "FP64", tau=0.8, shifting=False)
+    r, ux, uy, uz = L.rho_u()
+    assert np.abs(r - 1.0).max() < 1e-15 and not ux.any() and not uy.any() and not uz.any()
+    # unshifted 16-bit storage cannot even hold rest exactly (w_i are not FP16S values)
+    L = oracle.Lattice(3, 4, 5, "D3Q19", "SRT", "ORD32", "FP16S", tau=0.8, shifting=False)
+    r = L.rho_u()[0]
+    assert 0 < np.abs(r - 1.0).max() < 1e-3
+
+
+def test_outflow_needs_a_fluid_upstream_cell():
+    flags = np.zeros((2, 3, 4), dtype=np.uint8)
+    flags[1, 1, 2] = W.OUTFLOW
+    flags[1, 1, 1] = W.WALL
+    L = oracle.Lattice(4, 3, 2, "D3Q19", "SRT", "DEF64", "FP64")
+    with pytest.raises(ValueError):
+        L.set_geometry(flags)
+    flags[1, 1, 1] = 0
+    L.set_geometry(flags)
+
+
+def test_shifting_wins_back_sixteen_bit_accuracy():
+    """Sec. 2.2 / 4.2: with FP16 storage the unshifted populations (f near w)
+    lose the small deviations that carry the flow; the shifted ones keep
+    them.  2-D Taylor-Green vortex, velocity error against FP64 after 200 steps."""
+    n, u0, tau = 32, 0.01, 0.8
+    fields = W.taylor_green_extruded(n, u0, nz=1)
+    ref = oracle.Lattice(n, n, 1, "D2Q9", "SRT", "DEF64", "FP64", tau=tau)
+    ref.set_rho_u(*fields)
+    ref.step(200)
+    uref = np.stack(ref.rho_u()[1:3])
+    err = {}
+    for shifting in (True, False):
+        L = oracle.Lattice(n, n, 1, "D2Q9", "SRT", "ORD32", "FP16", tau=tau, shifting=shifting)
+        L.set_rho_u(*fields)
+        L.step(200)
+        u = np.stack(L.rho_u()[1:3])
+        err[shifting] = np.linalg.norm(u - uref) / np.linalg.norm(uref)
+    assert err[True] < 0.05
+    assert err[False] > 5 * err[True]

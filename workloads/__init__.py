@@ -170,6 +170,9 @@ def random_geometry(shape, seed, wall=0.08, moving=0.03, eq=0.02, outflow=0.02,
     fs = (r >= t) & (r < t + freeslip_frac)
     axes = rng.integers(0, 4, shape).astype(np.uint8)   # axis code 3: plain bounce-back
     flags[fs] = (WALL | FREESLIP | (axes << 5))[fs]
+    # an outflow cell pulls as if one cell upstream in x: keep that cell fluid
+    upstream_solid = (np.roll(flags, 1, axis=-1) & WALL) != 0
+    flags[((flags & OUTFLOW) != 0) & upstream_solid] = 0
     node_u = (u_amp * rng.uniform(-1, 1, (3,) + tuple(shape))).astype(np.float32)
     node_rho = (1.0 + 0.01 * rng.uniform(-1, 1, shape)).astype(np.float32)
     return flags, node_u, node_rho
