@@ -27,9 +27,10 @@ NVFLAGS = ARCH + [
     "-O3", "-std=c++17", "-lineinfo", "--fmad=false", "--expt-relaxed-constexpr",
     "-Xcompiler", "-fPIC,-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC,
 ]
-# (storage id, arithmetic) pairs: FP32 arithmetic for every format, FP64
-# arithmetic for FP64 and FP32 storage
-UNITS = [(f, 0) for f in range(10)] + [(0, 1), (1, 1)]
+# (storage id, arithmetic, velocity set) units: FP32 arithmetic for every
+# format, FP64 arithmetic for FP64 and FP32 storage; one unit per velocity
+# set keeps the units small enough to compile in parallel
+UNITS = [(f, 0, v) for f in range(10) for v in range(3)] + [(f, 1, v) for f in (0, 1) for v in range(3)]
 
 
 def _headers():
@@ -60,10 +61,10 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
         (os.path.join(CSRC, n), os.path.join(OUT, n[:-3] + ".o"), [])
         for n in sorted(os.listdir(CSRC)) if n.endswith(".cu") and n != "lbm_instantiate.cu"
     ]
-    for fmt, arith in UNITS:
+    for fmt, arith, vs in UNITS:
         jobs_list.append((os.path.join(CSRC, "lbm_instantiate.cu"),
-                          os.path.join(OUT, f"lbm_inst_{fmt}_{arith}.o"),
-                          [f"-DLBM_FMT={fmt}", f"-DLBM_ARITH={arith}"]))
+                          os.path.join(OUT, f"lbm_inst_{fmt}_{arith}_{vs}.o"),
+                          [f"-DLBM_FMT={fmt}", f"-DLBM_ARITH={arith}", f"-DLBM_VELSET={vs}"]))
 
     def stamp_of(job):
         src, _, defs = job

@@ -91,7 +91,7 @@ struct TempBuffer {
     lbm_handle* h;
     size_t bytes;
     void* p = nullptr;
-    TempBuffer(lbm_handle* hh, size_t b) : h(hh), bytes(b) { p = h->alloc(bytes); }
+    TempBuffer(lbm_handle* hh, size_t b) : h(hh), bytes(b) { p = bytes ? h->alloc(bytes) : nullptr; }
     ~TempBuffer() {
         if (p) {
             cudaStreamSynchronize(h->stream);
@@ -373,7 +373,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         }
         h->n_special = count;
     }
-    lbm_status st2 = ensure_layout(h);   // flags force the SoA layout
+    lbm_status st2 = ensure_layout(h);
     if (st2 != LBM_OK) return st2;
     st2 = zero_solid(h);                 // solid cells hold no populations
     if (st2 != LBM_OK) return st2;
@@ -459,7 +459,8 @@ lbm_status put_all(lbm_handle* h, const Relax<R>& k, int setf, int per_cell, Up 
         L.block = dim3(256);
         L.grid = dim3((unsigned)std::min<size_t>((count + 255) / 256, 152 * 32));
         L.stream = h->stream;
-        if (h->cuda(h->ks->put[h->aa() ? 1 : (h->chunked ? 2 : 0)](&pa, setf, L), "put kernel")) return LBM_ERR_CUDA;
+        if (h->cuda(h->ks->put[(h->aa() ? 1 : 0) | (h->chunked ? 2 : 0)](&pa, setf, L), "put kernel"))
+            return LBM_ERR_CUDA;
         if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
     }
     h->t = 0;
@@ -518,10 +519,10 @@ int staged_index(const lbm_handle* h) {
     return idx;
 }
 
-// the chunked layout: flag-free A-B lattice, 16-bit storage, nx a multiple of 64
+// the chunked layout: 16-bit storage, FP32 arithmetic, nx a multiple of 64
+// (A-B or A-A, with or without flags, any size)
 bool chunk_eligible(const lbm_handle* h) {
-    return !h->flags && !h->aa() && !h->fp64() && h->sb == 2 && (h->p.nx % lbm::CHUNK) == 0 && h->idx32() &&
-           h->ks->pair_chunked;
+    return !h->fp64() && h->sb == 2 && (h->p.nx % lbm::CHUNK) == 0 && h->ks->pair_chunked[0][0];
 }
 bool want_chunked(const lbm_handle* h) {
     return chunk_eligible(h) && (h->variant == LBM_VARIANT_AUTO || h->variant == LBM_VARIANT_PAIRED);
@@ -551,27 +552,33 @@ __global__ void k_relayout(const uint16_t* __restrict__ src, uint16_t* __restric
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
 #pragma unroll
         for (int i = 0; i < V::Q; ++i) {
-            const uint32_t soa = (uint32_t)i * N + n, ch = lbm::chunk_elem<V>(i, n);
+            const size_t soa = (size_t)i * N + n, ch = lbm::chunk_elem<V>(i, n);
             if (to_chunked) dst[ch] = src[soa];
             else dst[soa] = src[ch];
         }
     }
 }
 
-// zeroes the populations of solid cells (SoA layout)
+// zeroes the populations of solid cells (SoA, or chunked: element
+// ((n/64) q + i) 64 + n%64)
 template <class T>
-__global__ void k_zero_solid(const uint8_t* __restrict__ flags, T* f, int q, uint32_t N) {
+__global__ void k_zero_solid(const uint8_t* __restrict__ flags, T* f, int q, uint32_t N, int chunked) {
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
         if (flags[n] & lbm::F_WALL)
-            for (int i = 0; i < q; ++i) f[(size_t)i * N + n] = T(0);
+            for (int i = 0; i < q; ++i) {
+                const size_t e = chunked ? ((size_t)(n >> 6) * q + i) * lbm::CHUNK + (n & (lbm::CHUNK - 1))
+                                         : (size_t)i * N + n;
+                f[e] = T(0);
+            }
 }
 
 lbm_status zero_solid(lbm_handle* h) {
     const unsigned grid = (unsigned)std::min<size_t>((h->N + 255) / 256, 152 * 32);
     for (int c = 0; c < (h->aa() ? 1 : 2); ++c) {
-        if (h->sb == 8) k_zero_solid<double><<<grid, 256, 0, h->stream>>>(h->flags, (double*)h->f[c], h->q, (uint32_t)h->N);
-        else if (h->sb == 4) k_zero_solid<float><<<grid, 256, 0, h->stream>>>(h->flags, (float*)h->f[c], h->q, (uint32_t)h->N);
-        else k_zero_solid<uint16_t><<<grid, 256, 0, h->stream>>>(h->flags, (uint16_t*)h->f[c], h->q, (uint32_t)h->N);
+        const int ch = h->chunked;
+        if (h->sb == 8) k_zero_solid<double><<<grid, 256, 0, h->stream>>>(h->flags, (double*)h->f[c], h->q, (uint32_t)h->N, ch);
+        else if (h->sb == 4) k_zero_solid<float><<<grid, 256, 0, h->stream>>>(h->flags, (float*)h->f[c], h->q, (uint32_t)h->N, ch);
+        else k_zero_solid<uint16_t><<<grid, 256, 0, h->stream>>>(h->flags, (uint16_t*)h->f[c], h->q, (uint32_t)h->N, ch);
         if (h->cuda(cudaGetLastError(), "zero kernel")) return LBM_ERR_CUDA;
     }
     return LBM_OK;
@@ -581,15 +588,22 @@ lbm_status zero_solid(lbm_handle* h) {
 lbm_status ensure_layout(lbm_handle* h) {
     const int want = want_chunked(h) ? 1 : 0;
     if (want == h->chunked) return LBM_OK;
-    if (h->aa()) { h->chunked = 0; return LBM_OK; }
-    const uint16_t* src = (const uint16_t*)h->f[h->cur];
-    uint16_t* dst = (uint16_t*)h->f[1 - h->cur];
+    // A-B: into the other copy; A-A (one copy): through a transient copy of it
+    const size_t fbytes = (size_t)h->q * h->N * h->sb;
+    TempBuffer tmp(h, h->aa() ? fbytes : 0);
+    if (h->aa()) {
+        if (!tmp.p) return h->fail(LBM_ERR_OOM, "relayout buffer");
+        if (h->cuda(cudaMemcpyAsync(tmp.p, h->f[0], fbytes, cudaMemcpyDeviceToDevice, h->stream), "copy"))
+            return LBM_ERR_CUDA;
+    }
+    const uint16_t* src = h->aa() ? (const uint16_t*)tmp.p : (const uint16_t*)h->f[h->cur];
+    uint16_t* dst = h->aa() ? (uint16_t*)h->f[0] : (uint16_t*)h->f[1 - h->cur];
     const unsigned grid = (unsigned)std::min<size_t>((h->N + 255) / 256, 152 * 32);
     if (h->p.velset == LBM_D2Q9) k_relayout<D2Q9><<<grid, 256, 0, h->stream>>>(src, dst, (uint32_t)h->N, want);
     else if (h->p.velset == LBM_D3Q19) k_relayout<D3Q19><<<grid, 256, 0, h->stream>>>(src, dst, (uint32_t)h->N, want);
     else k_relayout<D3Q27><<<grid, 256, 0, h->stream>>>(src, dst, (uint32_t)h->N, want);
     if (h->cuda(cudaGetLastError(), "relayout kernel")) return LBM_ERR_CUDA;
-    h->cur = 1 - h->cur;
+    if (!h->aa()) h->cur = 1 - h->cur;
     h->chunked = want;
     return LBM_OK;
 }
@@ -604,7 +618,14 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
         L.block = dim3(32, 8, 1);
         L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
         L.stream = s;
-        st = h->cuda(h->ks->pair_chunked(&a, L), "chunked step kernel");
+        st = h->cuda(h->ks->pair_chunked[scheme][h->flags ? 1 : 0](&a, L), "chunked step kernel");
+        if (st == LBM_OK && h->flags && h->n_special > 0) {   // the non-plain cells
+            Launch B;
+            B.block = dim3(256);
+            B.grid = dim3((h->n_special + 255) / 256);
+            B.stream = s;
+            st = h->cuda(h->ks->list_chunked[scheme](&a, h->special, h->n_special, B), "list kernel");
+        }
     } else if (variant == LBM_VARIANT_PAIRED) {
         Launch L;
         L.block = dim3(h->bx, h->by, 1);

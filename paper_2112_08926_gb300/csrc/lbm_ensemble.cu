@@ -202,6 +202,12 @@ extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count,
         tiles_bound += (long long)h->N;   // at least one cell per tile
     }
     if (tiles_bound > 0x7FFFFFFFll) return LBM_ERR_UNSUPPORTED;
+    // the ensemble kernels address the structure-of-arrays layout
+    for (int k = 0; k < count; ++k)
+        if (members[k]->chunked) {
+            const lbm_status st = lbm_set_variant(members[k], LBM_VARIANT_GENERIC);
+            if (st != LBM_OK) return st;
+        }
     lbm_ensemble* e = new lbm_ensemble;
     e->m.assign(members, members + count);
     e->stream = h0->stream;

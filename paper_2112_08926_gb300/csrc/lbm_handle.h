@@ -94,8 +94,8 @@ struct lbm_handle {
     }
     int scheme_now() const { return !aa() ? lbm::SCHEME_AB : ((t & 1) ? lbm::SCHEME_AA_LOC : lbm::SCHEME_AA_PP); }
     int layout_now() const {
-        if (aa()) return (t & 1) ? lbm::LAYOUT_AA_NATURAL : lbm::LAYOUT_AA_SWAPPED;
-        return chunked ? lbm::LAYOUT_AB_CHUNKED : lbm::LAYOUT_AB;
+        const int phase = !aa() ? lbm::LAYOUT_AB : ((t & 1) ? lbm::LAYOUT_AA_NATURAL : lbm::LAYOUT_AA_SWAPPED);
+        return phase | (chunked ? lbm::LAYOUT_CHUNKED : 0);
     }
     Launch step_launch(cudaStream_t s) const {
         Launch L;

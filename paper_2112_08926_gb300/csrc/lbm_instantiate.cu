@@ -1,6 +1,7 @@
-// Instantiates every kernel for one storage format and arithmetic precision.
-// The build compiles this file once per pair with -DLBM_FMT=<storage id>
-// -DLBM_ARITH=<0 float | 1 double>, in parallel.
+// Instantiates every kernel for one storage format, arithmetic precision and
+// velocity set.  The build compiles this file once per triple with
+// -DLBM_FMT=<storage id> -DLBM_ARITH=<0 float | 1 double> -DLBM_VELSET=<0..2>,
+// in parallel.
 #include <type_traits>
 
 #include "lbm_kernels.cuh"
@@ -11,6 +12,9 @@
 #endif
 #ifndef LBM_ARITH
 #error "LBM_ARITH must be defined"
+#endif
+#ifndef LBM_VELSET
+#error "LBM_VELSET must be defined (0 D2Q9, 1 D3Q19, 2 D3Q27)"
 #endif
 
 namespace lbm {
@@ -26,9 +30,9 @@ cudaError_t launch_step(const void* args, const Launch& L) {
     return cudaGetLastError();
 }
 
-template <class V, int COLL, int SCHEME, class IX>
+template <class V, int COLL, int SCHEME, class IX, bool CH = false>
 cudaError_t launch_list(const void* args, const uint32_t* cells, uint32_t count, const Launch& L) {
-    k_step_list<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
+    k_step_list<V, COLL, FMT, Real, SCHEME, IX, CH><<<L.grid, L.block, 0, L.stream>>>(
         *static_cast<const StepArgs<Real>*>(args), cells, count);
     return cudaGetLastError();
 }
@@ -82,9 +86,10 @@ cudaError_t launch_pair(const void* args, const Launch& L) {
     return cudaGetLastError();
 }
 
-template <class V, int COLL>
+template <class V, int COLL, int PHASE, bool PLAIN>
 cudaError_t launch_pair_chunked(const void* args, const Launch& L) {
-    k_step_pair_chunked<V, COLL, FMT><<<L.grid, L.block, 0, L.stream>>>(*static_cast<const StepArgs<float>*>(args));
+    k_step_pair_chunked<V, COLL, FMT, PHASE, PLAIN><<<L.grid, L.block, 0, L.stream>>>(
+        *static_cast<const StepArgs<float>*>(args));
     return cudaGetLastError();
 }
 
@@ -106,13 +111,23 @@ void fill() {
     s.probe[LAYOUT_AB] = launch_probe<V, LAYOUT_AB>;
     s.probe[LAYOUT_AA_SWAPPED] = launch_probe<V, LAYOUT_AA_SWAPPED>;
     s.probe[LAYOUT_AA_NATURAL] = launch_probe<V, LAYOUT_AA_NATURAL>;
-    s.probe[LAYOUT_AB_CHUNKED] = launch_probe<V, LAYOUT_AB_CHUNKED>;
     s.put[0] = launch_put<V, 0>;
     s.put[1] = launch_put<V, 1>;
-    s.put[2] = launch_put<V, 2>;
-    if constexpr (LBM_ARITH == 0 && FMT >= 2) {
+    // the chunked layout and the paired kernels: 16-bit storage, FP32
+    // arithmetic; D3Q27 keeps the generic kernels (27 code pairs per lane do
+    // not fit the register budget of the paired kernels)
+    if constexpr (LBM_ARITH == 0 && FMT >= 2 && !std::is_same<V, D3Q27>::value) {
+        s.probe[LAYOUT_AB_CHUNKED] = launch_probe<V, LAYOUT_AB_CHUNKED>;
+        s.probe[LAYOUT_AA_SWAPPED_CHUNKED] = launch_probe<V, LAYOUT_AA_SWAPPED_CHUNKED>;
+        s.probe[LAYOUT_AA_NATURAL_CHUNKED] = launch_probe<V, LAYOUT_AA_NATURAL_CHUNKED>;
+        s.put[2] = launch_put<V, 2>;
+        s.put[3] = launch_put<V, 3>;
         s.pair = launch_pair<V, COLL>;
-        s.pair_chunked = launch_pair_chunked<V, COLL>;
+        static_for<0, 3>([&](auto PH) {
+            s.pair_chunked[PH.value][0] = launch_pair_chunked<V, COLL, PH.value, false>;
+            s.pair_chunked[PH.value][1] = launch_pair_chunked<V, COLL, PH.value, true>;
+            s.list_chunked[PH.value] = launch_list<V, COLL, PH.value, uint32_t, true>;
+        });
     }
     if constexpr (LBM_ARITH == 0 && FMT != 0 && std::is_same<V, D3Q19>::value) {
         s.staged[0] = launch_staged<V, COLL, 128>;
@@ -127,9 +142,9 @@ void fill() {
 
 struct Registrar {
     Registrar() {
-        fill<D2Q9, 0>(); fill<D2Q9, 1>();
-        fill<D3Q19, 0>(); fill<D3Q19, 1>();
-        fill<D3Q27, 0>(); fill<D3Q27, 1>();
+        if constexpr (LBM_VELSET == 0) { fill<D2Q9, 0>(); fill<D2Q9, 1>(); }
+        if constexpr (LBM_VELSET == 1) { fill<D3Q19, 0>(); fill<D3Q19, 1>(); }
+        if constexpr (LBM_VELSET == 2) { fill<D3Q27, 0>(); fill<D3Q27, 1>(); }
     }
 };
 const Registrar registrar;

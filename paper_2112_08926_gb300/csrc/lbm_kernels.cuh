@@ -20,16 +20,23 @@
 namespace lbm {
 
 enum { SCHEME_AB = 0, SCHEME_AA_PP = 1, SCHEME_AA_LOC = 2 };
-enum { LAYOUT_AB = 0, LAYOUT_AA_SWAPPED = 1, LAYOUT_AA_NATURAL = 2, LAYOUT_AB_CHUNKED = 3 };
+// Memory layouts: the phase of the streaming scheme (A-B, or the A-A slots
+// before an odd or an even step) in the low bits, LAYOUT_CHUNKED as a flag.
+enum {
+    LAYOUT_AB = 0, LAYOUT_AA_SWAPPED = 1, LAYOUT_AA_NATURAL = 2, LAYOUT_CHUNKED = 4,
+    LAYOUT_AB_CHUNKED = 4, LAYOUT_AA_SWAPPED_CHUNKED = 5, LAYOUT_AA_NATURAL_CHUNKED = 6
+};
+constexpr int layout_phase(int layout) { return layout & 3; }
+constexpr bool layout_chunked(int layout) { return (layout & LAYOUT_CHUNKED) != 0; }
 
-// Chunked (array-of-structure-of-arrays) layout of a flag-free A-B lattice
-// with nx a multiple of 64: the cells of a row are cut into chunks of 64
-// consecutive x; chunk c = n / 64 stores its q populations one after the
-// other, 64 codes each.  Element of population i of cell n:
+// Chunked (array-of-structure-of-arrays) layout of a 16-bit lattice with nx
+// a multiple of 64: the cells of a row are cut into chunks of 64 consecutive
+// x; chunk c = n / 64 stores its q populations (slots) one after the other,
+// 64 codes each.  Element of slot i of cell n:
 constexpr int CHUNK = 64;
 template <class V>
-__host__ __device__ __forceinline__ uint32_t chunk_elem(int i, uint32_t n) {
-    return ((n >> 6) * (uint32_t)V::Q + (uint32_t)i) * CHUNK + (n & (CHUNK - 1));
+__host__ __device__ __forceinline__ size_t chunk_elem(int i, uint32_t n) {
+    return ((size_t)(n >> 6) * (size_t)V::Q + (size_t)i) * CHUNK + (n & (CHUNK - 1));
 }
 enum { PROBE_FIELDS = 0, PROBE_F = 1, PROBE_REDUCE = 2 };
 
@@ -79,9 +86,11 @@ struct Nbr {
 // multiply-add; otherwise the slot's start (a product of kernel arguments
 // only, kept in uniform registers) is added to the 32-bit cell index, so
 // 64-bit lattices pay no 64-bit index arithmetic per thread.
-template <class IX, class T>
+// On the chunked layout (CH) the element is chunk_elem.
+template <class IX, bool CH, class V, class T>
 __device__ __forceinline__ T* elem_ptr(T* p, int slot, uint32_t N, uint32_t j) {
-    if constexpr (sizeof(IX) == 4) return p + ((uint32_t)slot * N + j);
+    if constexpr (CH) return p + chunk_elem<V>(slot, j);
+    else if constexpr (sizeof(IX) == 4) return p + ((uint32_t)slot * N + j);
     else return (p + (size_t)slot * (size_t)N) + j;
 }
 
@@ -101,7 +110,7 @@ __device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t
 // chosen with selects and all loads are issued before the moving-wall terms
 // are added, so the loads stay in flight together.
 // Returns the mask of directions whose upstream cell is solid (bit i).
-template <class V, int FMT, class R, bool AA, class IX>
+template <class V, int FMT, class R, bool AA, class IX, bool CH>
 __device__ __forceinline__ uint32_t gather_boundary(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
                                                     const Nbr& nb, R* f) {
     using S = Storage<FMT>;
@@ -131,7 +140,7 @@ __device__ __forceinline__ uint32_t gather_boundary(const StepArgs<R>& a, const 
                 cell = j2;
             }
         }
-        f[i] = S::template load_g<R>(elem_ptr<IX>(src, sl, N, cell), 0u);
+        f[i] = S::template load_g<R>(elem_ptr<IX, CH, V>(src, sl, N, cell), 0u);
     });
     uint32_t walls = 0;
     static_for<0, V::Q>([&](auto I) {
@@ -150,9 +159,11 @@ template <class V, int FMT, class R, bool FLAGS, int LAYOUT, class IX = size_t>
 __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename Storage<FMT>::T* src,
                                            int x, int y, int z, uint32_t n, uint32_t fl, R* f) {
     using S = Storage<FMT>;
-    if constexpr (LAYOUT == LAYOUT_AA_NATURAL) {
+    constexpr int PH = layout_phase(LAYOUT);
+    constexpr bool CH = layout_chunked(LAYOUT);
+    if constexpr (PH == LAYOUT_AA_NATURAL) {
         static_for<0, V::Q>([&](auto I) {
-            f[I.value] = S::template load_g<R>(elem_ptr<IX>(src, I.value, a.N, n), 0u);
+            f[I.value] = S::template load_g<R>(elem_ptr<IX, CH, V>(src, I.value, a.N, n), 0u);
         });
         if (FLAGS && (fl & F_NEAR_MOVING)) {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
@@ -161,23 +172,18 @@ __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename 
                 if (a.flags[j] & F_MOVING) f[I.value] = f[I.value] + moving_term<V, I.value, R, S::SL>(a.node_u, a.N, j);
             });
         }
-    } else if constexpr (LAYOUT == LAYOUT_AB_CHUNKED) {
-        const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
-        static_for<0, V::Q>([&](auto I) {
-            f[I.value] = S::template load_g<R>(src, chunk_elem<V>(I.value, nb.up<V, I.value>()));
-        });
     } else {
-        constexpr bool AA = LAYOUT == LAYOUT_AA_SWAPPED;
+        constexpr bool AA = PH == LAYOUT_AA_SWAPPED;
         if (FLAGS && (fl & F_NEAR_SOLID)) {
             int sx = x;
             if (!AA && (fl & F_OUTFLOW)) sx = x == 0 ? a.nx - 1 : x - 1;
             const Nbr nb(sx, y, z, a.nx, a.ny, a.nz);
-            return gather_boundary<V, FMT, R, AA, IX>(a, src, nb, f);
+            return gather_boundary<V, FMT, R, AA, IX, CH>(a, src, nb, f);
         } else {
             const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
             static_for<0, V::Q>([&](auto I) {
                 constexpr int slot = AA ? opposite(I.value) : I.value;
-                f[I.value] = S::template load_g<R>(elem_ptr<IX>(src, slot, a.N, nb.up<V, I.value>()), 0u);
+                f[I.value] = S::template load_g<R>(elem_ptr<IX, CH, V>(src, slot, a.N, nb.up<V, I.value>()), 0u);
             });
         }
     }
@@ -188,15 +194,17 @@ __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename 
 // flags): only cells whose flag byte is 0 -- fluid, no solid, moving or
 // equilibrium neighbour -- are updated; the others are left to the list
 // kernel, so no warp runs the boundary path for a few of its lanes.
-template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX, bool PLAIN_ONLY = false>
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX, bool PLAIN_ONLY = false,
+          bool CH = false>
 __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, int z) {
     using S = Storage<FMT>;
     using T = typename S::T;
     const uint32_t n = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * (uint32_t)z);
     const T* src = (const T*)a.src;
     T* dst = (T*)a.dst;
-    constexpr int LAYOUT = SCHEME == SCHEME_AB ? LAYOUT_AB
-                         : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
+    constexpr int PH = SCHEME == SCHEME_AB ? LAYOUT_AB
+                     : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
+    constexpr int LAYOUT = PH | (CH ? LAYOUT_CHUNKED : 0);
     const uint32_t fl = FLAGS ? (uint32_t)a.flags[n] : 0u;
     // The plain pull is issued for every cell together with the flag load,
     // so the two memory latencies overlap; solid and equilibrium cells drop
@@ -210,15 +218,15 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
         const R u[3] = {(R)a.node_u[n], (R)a.node_u[(size_t)a.N + n], (R)a.node_u[2 * (size_t)a.N + n]};
         equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f, a.k.sh);
     } else {
-        if (FLAGS && (fl & (LAYOUT == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
+        if (FLAGS && (fl & (PH == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
             walls = gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
         collide<V, COLL, R, S::SL>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
-        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(elem_ptr<IX>(dst, I.value, a.N, n), 0u, f[I.value]); });
+        static_for<0, V::Q>([&](auto I) { S::template store_g<R>(elem_ptr<IX, CH, V>(dst, I.value, a.N, n), 0u, f[I.value]); });
     } else if constexpr (SCHEME == SCHEME_AA_LOC) {
         static_for<0, V::Q>([&](auto I) {
-            S::template store_g<R>(elem_ptr<IX>(dst, opposite(I.value), a.N, n), 0u, f[I.value]);
+            S::template store_g<R>(elem_ptr<IX, CH, V>(dst, opposite(I.value), a.N, n), 0u, f[I.value]);
         });
     } else {
         const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
@@ -228,11 +236,11 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
                 const uint32_t d = nb.down<V, i>();
                 // the downstream cell of i is the upstream cell of opposite(i)
                 const bool wall = (walls >> opposite(i)) & 1u;   // reflected back into this cell
-                S::template store_g<R>(elem_ptr<IX>(dst, wall ? opposite(i) : i, a.N, wall ? n : d), 0u, f[i]);
+                S::template store_g<R>(elem_ptr<IX, CH, V>(dst, wall ? opposite(i) : i, a.N, wall ? n : d), 0u, f[i]);
             });
         } else {
             static_for<0, V::Q>([&](auto I) {
-                S::template store_g<R>(elem_ptr<IX>(dst, I.value, a.N, nb.down<V, I.value>()), 0u, f[I.value]);
+                S::template store_g<R>(elem_ptr<IX, CH, V>(dst, I.value, a.N, nb.down<V, I.value>()), 0u, f[I.value]);
             });
         }
     }
@@ -242,7 +250,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
 // FLAGS: the lattice has flags; then this kernel updates the plain cells
 // (flag byte 0) only and k_step_list the listed others.
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
-__global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : 3) k_step(const StepArgs<R> a) {
+__global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : (FLAGS ? 3 : 4)) k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 
 // The non-plain cells of a flagged lattice (solid cells excluded): boundary
 // neighbours, equilibrium and outflow cells, from a list built when the
 // geometry is set, one per thread.
-template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX, bool CH>
 __global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : 3)
     k_step_list(const StepArgs<R> a, const uint32_t* __restrict__ cells, uint32_t count) {
     const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,7 +269,7 @@ __global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 
     const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
     const uint32_t z = n / plane, r = n - z * plane;
     const uint32_t y = r / (uint32_t)a.nx, x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, true, IX>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, CH>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- staged kernel
@@ -489,14 +497,26 @@ template <int FMT> struct PairCodecHalf {
 template <> struct PairCodec<2> : PairCodecHalf<2> {};
 template <> struct PairCodec<3> : PairCodecHalf<3> {};
 
-// Flag-free periodic A-B step on the chunked layout, 16-bit storage: a warp
+// One step on the chunked layout, 16-bit storage, FP32 arithmetic: a warp
 // owns one 64-cell chunk of a row (lane l: cells 2l and 2l+1) and moves every
 // population as one 128-byte line of 32-bit code pairs, at a compile-time
-// offset from the chunk of the source row.  Pairs shifted in x are assembled
-// by warp shuffles; lanes 0 and 31 read the missing code from the
-// neighbouring chunk (periodic in x).  Block = 32 x by threads; needs nx a
-// multiple of 64 and q*N < 2^32.  Per-cell arithmetic is cell_step's.
-template <class V, int COLL, int FMT>
+// offset from the chunk of the source (or destination) row.  Needs nx a
+// multiple of 64; block = 32 x by threads.  Per-cell arithmetic is
+// cell_step's.
+//   PHASE LAYOUT_AB: pull from copy A, write own cells in copy B.  Pairs
+//     shifted in x are assembled by warp shuffles; lanes 0 and 31 read the
+//     missing code from the neighbouring chunk (periodic in x).
+//   PHASE LAYOUT_AA_SWAPPED (odd A-A half): pull slot opposite(i) of the
+//     upstream cell the same way, push slot i of the downstream cell: a pair
+//     shifted in x is assembled from this lane's and the neighbouring lane's
+//     codes; the half that belongs to the neighbouring chunk is one 16-bit
+//     store (every location is written by the warp whose cell read it).
+//   PHASE LAYOUT_AA_NATURAL (even A-A half): read own slot i, write own slot
+//     opposite(i); no shifts.
+// PLAIN (flagged lattice): only cells whose flag byte is 0 are written; a
+// pair with one such cell is written as a single 16-bit code; the other
+// cells belong to the list kernel.
+template <class V, int COLL, int FMT, int PHASE, bool PLAIN>
 __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<float> a) {
     using PC = PairCodec<FMT>;
     constexpr int SL = Codec16<FMT>::SL;
@@ -514,41 +534,93 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
     const int32_t prev = X == 0 ? (int32_t)((XT - 1) * CHE) : -(int32_t)CHE;
     const int32_t next = X == XT - 1 ? -(int32_t)((XT - 1) * CHE) : (int32_t)CHE;
     const uint16_t* src = (const uint16_t*)a.src;
-    // lane 0 reads code 63 of the previous chunk, lane 31 code 0 of the next one
-    const int32_t adj = lane == 0 ? prev + (CHUNK - 1) : next;
+    uint16_t* dst = (uint16_t*)a.dst;
+    const uint32_t own_chunk = (ry[1] + rz[1]) * XT + X;   // < 2^25: N < 2^31 cells
+    uint32_t pl = 3u;   // bit 0: cell 2l is plain, bit 1: cell 2l + 1
+    if constexpr (PLAIN) {
+        const uint32_t fl2 = reinterpret_cast<const uint16_t*>(a.flags)[own_chunk * (CHUNK / 2) + lane];
+        pl = ((fl2 & 0xFFu) == 0u ? 1u : 0u) | ((fl2 >> 8) == 0u ? 2u : 0u);
+        if (!__any_sync(0xffffffffu, pl != 0u)) return;   // nothing plain in this chunk
+    }
     uint32_t g[V::Q];   // lo half: cell 2*lane, hi half: cell 2*lane + 1 (of this chunk)
-    // loads grouped by source row (c_y, c_z): one 64-bit pointer per row, the
-    // population offsets i*CHUNK are compile-time
-    static_for<0, 9>([&](auto RC) {
-        constexpr int cyr = RC.value % 3 - 1, czr = RC.value / 3 - 1;
-        const uint16_t* rowp = src + ((ry[1 - cyr] + rz[1 - czr]) * XT + X) * CHE;
-        const uint32_t* pairs = reinterpret_cast<const uint32_t*>(rowp) + lane;
-        const uint16_t* edge = rowp + adj;
-        static_for<0, V::Q>([&](auto I) {
-            constexpr int i = I.value, cx = V::c(i, 0);
-            if constexpr (V::c(i, 1) == cyr && V::c(i, 2) == czr) {
-                const uint32_t P = pairs[i * (CHUNK / 2)];
-                if constexpr (cx == 0) {
-                    g[i] = P;
-                } else if constexpr (cx > 0) {      // sources 2l-1, 2l
-                    const uint32_t Pu = __shfl_up_sync(0xffffffffu, P, 1);
-                    const uint32_t e = lane == 0 ? (uint32_t)edge[i * CHUNK] : (Pu >> 16);
-                    g[i] = (P << 16) | e;
-                } else {                            // sources 2l+1, 2l+2
-                    const uint32_t Pd = __shfl_down_sync(0xffffffffu, P, 1);
-                    const uint32_t e = lane == 31 ? (uint32_t)edge[i * CHUNK] : (Pd & 0xFFFFu);
-                    g[i] = (P >> 16) | (e << 16);
+    if constexpr (PHASE == LAYOUT_AA_NATURAL) {
+        const uint32_t* pairs = reinterpret_cast<const uint32_t*>(src + (size_t)own_chunk * CHE) + lane;
+        static_for<0, V::Q>([&](auto I) { g[I.value] = pairs[I.value * (CHUNK / 2)]; });
+    } else {
+        // lane 0 reads code 63 of the previous chunk, lane 31 code 0 of the next one
+        const int32_t adj = lane == 0 ? prev + (CHUNK - 1) : next;
+        // loads grouped by source row (c_y, c_z): one pointer per row, the slot
+        // offsets are compile-time
+        static_for<0, 9>([&](auto RC) {
+            constexpr int cyr = RC.value % 3 - 1, czr = RC.value / 3 - 1;
+            const uint16_t* rowp = src + (size_t)((ry[1 - cyr] + rz[1 - czr]) * XT + X) * CHE;
+            const uint32_t* pairs = reinterpret_cast<const uint32_t*>(rowp) + lane;
+            const uint16_t* edge = rowp + adj;
+            static_for<0, V::Q>([&](auto I) {
+                constexpr int i = I.value, cx = V::c(i, 0);
+                constexpr int slot = PHASE == LAYOUT_AA_SWAPPED ? opposite(i) : i;
+                if constexpr (V::c(i, 1) == cyr && V::c(i, 2) == czr) {
+                    const uint32_t P = pairs[slot * (CHUNK / 2)];
+                    if constexpr (cx == 0) {
+                        g[i] = P;
+                    } else if constexpr (cx > 0) {      // sources 2l-1, 2l
+                        const uint32_t Pu = __shfl_up_sync(0xffffffffu, P, 1);
+                        const uint32_t e = lane == 0 ? (uint32_t)edge[slot * CHUNK] : (Pu >> 16);
+                        g[i] = (P << 16) | e;
+                    } else {                            // sources 2l+1, 2l+2
+                        const uint32_t Pd = __shfl_down_sync(0xffffffffu, P, 1);
+                        const uint32_t e = lane == 31 ? (uint32_t)edge[slot * CHUNK] : (Pd & 0xFFFFu);
+                        g[i] = (P >> 16) | (e << 16);
+                    }
                 }
-            }
+            });
         });
-    });
+    }
     float fa[V::Q], fb[V::Q];
     static_for<0, V::Q>([&](auto I) { fa[I.value] = PC::dec(g[I.value]).x; });
     collide<V, COLL, float, SL>(a.k, fa);
     static_for<0, V::Q>([&](auto I) { fb[I.value] = PC::dec(g[I.value]).y; });
     collide<V, COLL, float, SL>(a.k, fb);
-    uint32_t* out = reinterpret_cast<uint32_t*>((uint16_t*)a.dst + ((ry[1] + rz[1]) * XT + X) * CHE) + lane;
-    static_for<0, V::Q>([&](auto I) { out[I.value * (CHUNK / 2)] = PC::enc(fa[I.value], fb[I.value]); });
+    // writes the pair w of 16-bit codes at element e (of line start `line`),
+    // only the halves whose cells may be written (ok bit 0: lo, bit 1: hi)
+    auto put = [&](uint16_t* line, int e, uint32_t w, uint32_t ok) {
+        if (ok == 3u) *reinterpret_cast<uint32_t*>(line + e) = w;
+        else if (ok == 1u) line[e] = (uint16_t)w;
+        else if (ok == 2u) line[e + 1] = (uint16_t)(w >> 16);
+    };
+    if constexpr (PHASE != LAYOUT_AA_SWAPPED) {
+        uint16_t* out = dst + (size_t)own_chunk * CHE + 2 * lane;
+        static_for<0, V::Q>([&](auto I) {
+            constexpr int slot = PHASE == LAYOUT_AA_NATURAL ? opposite(I.value) : I.value;
+            const uint32_t w = PC::enc(fa[I.value], fb[I.value]);
+            if constexpr (PLAIN) put(out + slot * CHUNK, 0, w, pl);
+            else *reinterpret_cast<uint32_t*>(out + slot * CHUNK) = w;
+        });
+    } else {
+        // push slot i into the destination row (y + c_y, z + c_z)
+        const uint32_t pl_up = __shfl_up_sync(0xffffffffu, pl, 1), pl_dn = __shfl_down_sync(0xffffffffu, pl, 1);
+        static_for<0, V::Q>([&](auto I) {
+            constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
+            uint16_t* rowp = dst + (size_t)((ry[1 + cy] + rz[1 + cz]) * XT + X) * CHE + i * CHUNK;
+            const uint32_t own = PC::enc(fa[i], fb[i]);
+            if constexpr (cx == 0) {
+                if constexpr (PLAIN) put(rowp, 2 * lane, own, pl);
+                else *reinterpret_cast<uint32_t*>(rowp + 2 * lane) = own;
+            } else if constexpr (cx > 0) {            // cells 2l-1, 2l land on 2l, 2l+1
+                const uint32_t up = __shfl_up_sync(0xffffffffu, own, 1);
+                const uint32_t w = __byte_perm(up, own, 0x5432);
+                const uint32_t ok = (lane == 0 ? 0u : ((pl_up >> 1) & 1u)) | ((pl & 1u) << 1);
+                put(rowp, 2 * lane, w, ok);
+                if (lane == 31 && (pl & 2u)) rowp[next + 0] = (uint16_t)(own >> 16);   // cell 63 -> next chunk
+            } else {                                  // cells 2l+1, 2l+2 land on 2l, 2l+1
+                const uint32_t dn = __shfl_down_sync(0xffffffffu, own, 1);
+                const uint32_t w = __byte_perm(own, dn, 0x5432);
+                const uint32_t ok = ((pl >> 1) & 1u) | (lane == 31 ? 0u : ((pl_dn & 1u) << 1));
+                put(rowp, 2 * lane, w, ok);
+                if (lane == 0 && (pl & 1u)) rowp[prev + (CHUNK - 1)] = (uint16_t)own;   // cell 0 -> previous chunk
+            }
+        });
+    }
 }
 
 // ---------------------------------------------------------------- ensemble
@@ -705,9 +777,11 @@ template <class R> struct PutArgs {
     const double* in[4];
 };
 
-template <class V, int FMT, class R, int PUT_LAYOUT>   // 0: A-B, 1: A-A (swapped slots), 2: A-B chunked
+// PUT_LAYOUT bit 0: A-A (swapped slots), bit 1: chunked
+template <class V, int FMT, class R, int PUT_LAYOUT>
 __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
-    constexpr bool AA = PUT_LAYOUT == 1;
+    constexpr bool AA = (PUT_LAYOUT & 1) != 0;
+    constexpr bool CH = (PUT_LAYOUT & 2) != 0;
     using S = Storage<FMT>;
     const StepArgs<R>& a = p.a;
     const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
@@ -727,7 +801,7 @@ __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
         }
         static_for<0, V::Q>([&](auto I) {
             constexpr int slot = AA ? opposite(I.value) : I.value;
-            const size_t e = PUT_LAYOUT == 2 ? (size_t)chunk_elem<V>(I.value, n) : (size_t)slot * a.N + n;
+            const size_t e = CH ? (size_t)chunk_elem<V>(slot, n) : (size_t)slot * a.N + n;
             S::template store<R>(dst, e, solid ? R(0) : f[I.value]);
         });
     }

@@ -26,14 +26,15 @@ using StagedFn = cudaError_t (*)(const void* step_args, int grid, int tiles_y, i
 struct KernelSet {
     StepFn step[3][2][2] = {};   // [scheme: AB, AA_PP, AA_LOC][flags][32-bit indices]
     ListFn list[3][2] = {};      // [scheme][32-bit indices]: the non-plain cells of a flagged lattice
+    ListFn list_chunked[3] = {}; // [scheme]: the same on the chunked layout
     EnsFn ens[3][2] = {};        // [scheme][32-bit indices], flags always on: plain cells
     EnsListFn ens_list[3][2] = {};   // the listed non-plain cells of all members
-    ProbeFn probe[4] = {};    // [layout: AB, AA swapped, AA natural, AB chunked]
-    PutFn put[3] = {};        // [A-B, A-A, A-B chunked]
+    ProbeFn probe[8] = {};    // [layout code: phase | 4 if chunked]
+    PutFn put[4] = {};        // [bit 0: A-A, bit 1: chunked]
     StagedFn staged[3] = {};  // row length 128, 256, 512 (D3Q19, FP32 arithmetic only)
     int staged_rows[3] = {};  // rows per tile
     StepFn pair = nullptr;    // two cells per thread (flag-free A-B, 16-bit storage)
-    StepFn pair_chunked = nullptr;   // the same on the chunked layout
+    StepFn pair_chunked[3][2] = {};  // chunked layout: [phase: A-B, A-A odd, A-A even][plain cells only]
     bool present = false;
 };
 
