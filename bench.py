@@ -226,7 +226,7 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
                         f"tau U[0.51,0.9], lid U[0.02,0.1], FP32/FP16S, A-B",
             "cells": cells, "steps": steps, "tile": [bx, by],
             "batched_mlups": cells * steps / t_b / 1e6, "per_launch_mlups": cells * steps / t_e / 1e6,
-            "speedup": t_e / t_b, "launches_per_step": {"batched": 1, "per_launch": count}}
+            "speedup": t_e / t_b, "launches_per_step": {"batched": 2, "per_launch": 2 * count}}
 
 
 def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1, only=None):

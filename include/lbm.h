@@ -277,10 +277,12 @@ typedef struct lbm_ensemble lbm_ensemble;
  * the ensemble adds a device descriptor table and a per-tile member table.
  * All launches go to the first member's stream. */
 lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out);
-/* Advance every member nsteps steps: one launch per step over all members,
- * replayed from a CUDA graph of up to 64 steps. */
+/* Advance every member nsteps steps: per step one launch over the plain
+ * cells of all members and one over the listed boundary cells of all
+ * members, replayed from a CUDA graph of up to 64 steps. */
 lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps);
-/* Same result, one launch per member per step (the baseline). */
+/* Same result, member by member (two launches per member per step: the
+ * baseline). */
 lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps);
 /* Cells per tile (thread block) of the ensemble launch: bx a multiple of 32
  * in [32, 256], by must be 1 (tiles are runs of consecutive cells). */

@@ -237,6 +237,24 @@ extern "C" lbm_status lbm_set_block(lbm_handle* h, int bx, int by) {
 
 namespace {
 
+// Lists the non-solid cells whose flag byte is not 0 (after the internal
+// neighbour bits are set).  count[0] must start at 0; with out == NULL only
+// counts.  One atomic per warp; a warp's cells keep their order.
+__global__ void k_list_special(const uint8_t* __restrict__ flags, size_t N, uint32_t* count, uint32_t* out) {
+    const int lane = threadIdx.x & 31;
+    for (size_t base = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(size_t)31; base < N;
+         base += (size_t)gridDim.x * blockDim.x) {
+        const size_t n = base + lane;
+        const uint32_t fl = n < N ? flags[n] : 0u;
+        const bool sp = fl != 0u && !(fl & F_WALL);
+        const uint32_t mask = __ballot_sync(0xffffffffu, sp);
+        uint32_t at = 0;
+        if (lane == 0 && mask) at = atomicAdd(count, (uint32_t)__popc(mask));
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if (sp && out) out[at + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)n;
+    }
+}
+
 __global__ void k_fill(float* p, size_t n, float v) {
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) p[i] = v;
 }
@@ -260,6 +278,9 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
     if (st != LBM_OK) return st;
     const size_t N = h->N;
     if (!flags) {
+        h->release((void*&)h->special, (size_t)h->special_cap * sizeof(uint32_t));
+        h->special_cap = 0;
+        h->n_special = 0;
         h->release((void*&)h->flags, N);
         h->release((void*&)h->node_u, 3 * N * sizeof(float));
         h->release((void*&)h->node_rho, N * sizeof(float));
@@ -328,6 +349,29 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         else if (h->p.velset == LBM_D3Q19) k_mark_neighbours<D3Q19><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
         else k_mark_neighbours<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
         if (h->cuda(cudaGetLastError(), "mark kernel")) return LBM_ERR_CUDA;
+    }
+    {   // list of the non-plain cells (two passes: count, then fill)
+        h->release((void*&)h->special, (size_t)h->special_cap * sizeof(uint32_t));
+        h->special_cap = 0;
+        h->n_special = 0;
+        uint32_t* cnt = reinterpret_cast<uint32_t*>(h->partial);   // scratch word pair
+        const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
+        if (h->cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), h->stream), "memset")) return LBM_ERR_CUDA;
+        k_list_special<<<grid, 256, 0, h->stream>>>(h->flags, N, cnt, nullptr);
+        if (h->cuda(cudaGetLastError(), "list kernel")) return LBM_ERR_CUDA;
+        uint32_t count = 0;
+        if (h->cuda(cudaMemcpyAsync(&count, cnt, sizeof count, cudaMemcpyDeviceToHost, h->stream), "download") ||
+            h->cuda(cudaStreamSynchronize(h->stream), "sync"))
+            return LBM_ERR_CUDA;
+        if (count > 0) {
+            h->special = (uint32_t*)h->alloc((size_t)count * sizeof(uint32_t));
+            if (!h->special) return h->fail(LBM_ERR_OOM, "cell list");
+            h->special_cap = count;
+            if (h->cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), h->stream), "memset")) return LBM_ERR_CUDA;
+            k_list_special<<<grid, 256, 0, h->stream>>>(h->flags, N, cnt, h->special);
+            if (h->cuda(cudaGetLastError(), "list kernel")) return LBM_ERR_CUDA;
+        }
+        h->n_special = count;
     }
     lbm_status st2 = ensure_layout(h);
     if (st2 != LBM_OK) return st2;
@@ -575,6 +619,13 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
         L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
         L.stream = s;
         st = h->cuda(h->ks->pair_chunked[scheme][h->flags ? 1 : 0](&a, L), "chunked step kernel");
+        if (st == LBM_OK && h->flags && h->n_special > 0) {   // the non-plain cells
+            Launch B;
+            B.block = dim3(256);
+            B.grid = dim3((h->n_special + 255) / 256);
+            B.stream = s;
+            st = h->cuda(h->ks->list_chunked[scheme](&a, h->special, h->n_special, B), "list kernel");
+        }
     } else if (variant == LBM_VARIANT_PAIRED) {
         Launch L;
         L.block = dim3(h->bx, h->by, 1);
@@ -590,6 +641,13 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
     } else {
         st = h->cuda(h->ks->step[scheme][h->flags ? 1 : 0][h->idx32() ? 1 : 0](&a, h->step_launch(s)),
                      "step kernel");
+        if (st == LBM_OK && h->flags && h->n_special > 0) {   // the non-plain cells
+            Launch L;
+            L.block = dim3(256);
+            L.grid = dim3((h->n_special + 255) / 256);
+            L.stream = s;
+            st = h->cuda(h->ks->list[scheme][h->idx32() ? 1 : 0](&a, h->special, h->n_special, L), "list kernel");
+        }
     }
     if (st != LBM_OK) return st;
     if (!h->aa()) h->cur ^= 1;

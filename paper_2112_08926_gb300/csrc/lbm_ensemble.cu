@@ -27,6 +27,8 @@ struct lbm_ensemble {
     KernelSet* ks = nullptr;
     bool fp64 = false, aa = false;
     void* table = nullptr;          // EnsMember<R>[count]
+    uint64_t* list = nullptr;       // non-plain cells of all members: member << 32 | cell
+    uint32_t n_list = 0;
     uint32_t* tile_member = nullptr;
     size_t table_bytes = 0, tiles_alloc = 0;
     int total_tiles = 0;
@@ -49,6 +51,11 @@ struct lbm_ensemble {
 };
 
 namespace {
+
+__global__ void k_tag_cells(const uint32_t* __restrict__ cells, uint32_t count, uint32_t member, uint64_t* out) {
+    for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
+        out[t] = ((uint64_t)member << 32) | cells[t];
+}
 
 // floor(n / d) = umulhi(n, magic) >> shift for every n < 2^31 (d >= 2):
 // shift + 32 = 31 + ceil(log2 d), magic = ceil(2^(31 + ceil(log2 d)) / d)
@@ -113,6 +120,24 @@ lbm_status upload_table(lbm_ensemble* e) {
     if (e->cuda(cudaMemcpyAsync(e->tile_member, tiles.data(), tiles.size() * sizeof(uint32_t),
                                 cudaMemcpyHostToDevice, e->stream), "table upload"))
         return LBM_ERR_CUDA;
+    if (!e->list) {   // the members' lists of non-plain cells, concatenated
+        size_t total = 0;
+        for (lbm_handle* h : e->m) total += h->n_special;
+        if (total > 0xFFFFFFFFull) return LBM_ERR_UNSUPPORTED;
+        if (total > 0) {
+            if (e->cuda(cudaMalloc((void**)&e->list, total * sizeof(uint64_t)), "list alloc")) return LBM_ERR_OOM;
+            size_t at = 0;
+            for (size_t k = 0; k < e->m.size(); ++k) {
+                const lbm_handle* h = e->m[k];
+                if (!h->n_special) continue;
+                k_tag_cells<<<(unsigned)std::min<size_t>((h->n_special + 255) / 256, 1024), 256, 0, e->stream>>>(
+                    h->special, h->n_special, (uint32_t)k, e->list + at);
+                if (e->cuda(cudaGetLastError(), "list kernel")) return LBM_ERR_CUDA;
+                at += h->n_special;
+            }
+        }
+        e->n_list = (uint32_t)total;
+    }
     if (e->cuda(cudaStreamSynchronize(e->stream), "sync")) return LBM_ERR_CUDA;
     e->drop_graphs();
     return LBM_OK;
@@ -127,7 +152,15 @@ lbm_status launch(lbm_ensemble* e, int64_t s, cudaStream_t stream) {
     const int64_t t = e->t0[0] + s;
     const int scheme = !e->aa ? SCHEME_AB : ((t & 1) ? SCHEME_AA_LOC : SCHEME_AA_PP);
     const int parity = e->aa ? 0 : (int)(s & 1);
-    return e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L), "ensemble kernel");
+    lbm_status st = e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L),
+                            "ensemble kernel");
+    if (st != LBM_OK || e->n_list == 0) return st;
+    Launch B;
+    B.block = dim3(256, 1, 1);
+    B.grid = dim3((e->n_list + 255) / 256, 1, 1);
+    B.stream = stream;
+    return e->cuda(e->ks->ens_list[scheme][e->idx32 ? 1 : 0](e->table, e->list, e->n_list, parity, B),
+                   "ensemble list kernel");
 }
 
 lbm_status check_members(lbm_ensemble* e) {
@@ -204,6 +237,7 @@ extern "C" lbm_status lbm_ensemble_destroy(lbm_ensemble* e) {
     e->drop_graphs();
     if (e->table) cudaFree(e->table);
     if (e->tile_member) cudaFree(e->tile_member);
+    if (e->list) cudaFree(e->list);
     if (e->capture) cudaStreamDestroy(e->capture);
     delete e;
     return LBM_OK;

@@ -29,6 +29,8 @@ struct lbm_handle {
     float* node_rho = nullptr;
     double* scratch = nullptr;
     size_t scratch_doubles = 0;
+    uint32_t* special = nullptr;   // cells that are not plain fluid (flagged lattices)
+    uint32_t n_special = 0, special_cap = 0;
     double* partial = nullptr;
     int64_t t = 0;
     int cur = 0;

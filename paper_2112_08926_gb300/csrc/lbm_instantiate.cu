@@ -30,10 +30,24 @@ cudaError_t launch_step(const void* args, const Launch& L) {
     return cudaGetLastError();
 }
 
+template <class V, int COLL, int SCHEME, class IX, bool CH = false>
+cudaError_t launch_list(const void* args, const uint32_t* cells, uint32_t count, const Launch& L) {
+    k_step_list<V, COLL, FMT, Real, SCHEME, IX, CH><<<L.grid, L.block, 0, L.stream>>>(
+        *static_cast<const StepArgs<Real>*>(args), cells, count);
+    return cudaGetLastError();
+}
+
 template <class V, int COLL, int SCHEME, class IX>
 cudaError_t launch_ens(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
     k_ensemble_step<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
         static_cast<const EnsMember<Real>*>(members), tile_member, parity);
+    return cudaGetLastError();
+}
+
+template <class V, int COLL, int SCHEME, class IX>
+cudaError_t launch_ens_list(const void* members, const uint64_t* cells, uint32_t count, int parity, const Launch& L) {
+    k_ensemble_list<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
+        static_cast<const EnsMember<Real>*>(members), cells, count, parity);
     return cudaGetLastError();
 }
 
@@ -87,8 +101,12 @@ void fill() {
         s.step[SC.value][1][0] = launch_step<V, COLL, SC.value, true, size_t>;
         s.step[SC.value][0][1] = launch_step<V, COLL, SC.value, false, uint32_t>;
         s.step[SC.value][1][1] = launch_step<V, COLL, SC.value, true, uint32_t>;
+        s.list[SC.value][0] = launch_list<V, COLL, SC.value, size_t>;
+        s.list[SC.value][1] = launch_list<V, COLL, SC.value, uint32_t>;
         s.ens[SC.value][0] = launch_ens<V, COLL, SC.value, size_t>;
         s.ens[SC.value][1] = launch_ens<V, COLL, SC.value, uint32_t>;
+        s.ens_list[SC.value][0] = launch_ens_list<V, COLL, SC.value, size_t>;
+        s.ens_list[SC.value][1] = launch_ens_list<V, COLL, SC.value, uint32_t>;
     });
     s.probe[LAYOUT_AB] = launch_probe<V, LAYOUT_AB>;
     s.probe[LAYOUT_AA_SWAPPED] = launch_probe<V, LAYOUT_AA_SWAPPED>;
@@ -108,6 +126,7 @@ void fill() {
         static_for<0, 3>([&](auto PH) {
             s.pair_chunked[PH.value][0] = launch_pair_chunked<V, COLL, PH.value, false>;
             s.pair_chunked[PH.value][1] = launch_pair_chunked<V, COLL, PH.value, true>;
+            s.list_chunked[PH.value] = launch_list<V, COLL, PH.value, uint32_t, true>;
         });
     }
     if constexpr (LBM_ARITH == 0 && FMT != 0 && std::is_same<V, D3Q19>::value) {

@@ -246,54 +246,30 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     }
 }
 
-// Boundary cells deferred within a block.  A flagged lattice updates its
-// plain cells (flag byte 0) in the kernels' fast paths; every other
-// non-solid cell of the block (next to a wall, equilibrium or outflow) is
-// queued in shared memory and updated after the block's plain cells, densely
-// by the block's threads, so no warp runs the boundary path for a few of its
-// lanes and the lines around the queued cells were just read by the block.
-struct CellQueue {
-    uint32_t* cells;
-    uint32_t* count;
-    __device__ __forceinline__ void push(uint32_t n) { cells[atomicAdd(count, 1u)] = n; }
-};
-__device__ __forceinline__ bool is_deferred(uint32_t fl) { return fl != 0u && !(fl & F_WALL); }
-
-template <class V, int COLL, int FMT, class R, int SCHEME, class IX, bool CH>
-__device__ __forceinline__ void run_queue(const StepArgs<R>& a, const uint32_t* cells, uint32_t count) {
-    const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
-    const uint32_t nthr = blockDim.x * blockDim.y;
-    for (uint32_t t = threadIdx.x + blockDim.x * threadIdx.y; t < count; t += nthr) {
-        const uint32_t n = cells[t];
-        const uint32_t z = n / plane, r = n - z * plane;
-        const uint32_t y = r / (uint32_t)a.nx, x = r - y * (uint32_t)a.nx;
-        cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, CH>(a, (int)x, (int)y, (int)z);
-    }
-}
-
 // IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic).
-// FLAGS: the lattice has flags (boundary cells deferred, see CellQueue).
-// Blocks have at most 256 threads.
+// FLAGS: the lattice has flags; then this kernel updates the plain cells
+// (flag byte 0) only and k_step_list the listed others.
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
 __global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : (FLAGS ? 3 : 4)) k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool in = x < a.nx && y < a.ny;
-    if constexpr (!FLAGS) {
-        if (in) cell_step<V, COLL, FMT, R, SCHEME, false, IX>(a, x, y, (int)blockIdx.z);
-    } else {
-        __shared__ uint32_t qcells[256];
-        __shared__ uint32_t qcount;
-        if (threadIdx.x == 0 && threadIdx.y == 0) qcount = 0u;
-        __syncthreads();
-        if (in) {
-            const uint32_t n = (uint32_t)x + (uint32_t)a.nx * ((uint32_t)y + (uint32_t)a.ny * blockIdx.z);
-            if (is_deferred(a.flags[n])) CellQueue{qcells, &qcount}.push(n);
-            cell_step<V, COLL, FMT, R, SCHEME, true, IX, true>(a, x, y, (int)blockIdx.z);
-        }
-        __syncthreads();
-        run_queue<V, COLL, FMT, R, SCHEME, IX, false>(a, qcells, qcount);
-    }
+    if (x >= a.nx || y >= a.ny) return;
+    cell_step<V, COLL, FMT, R, SCHEME, FLAGS, IX, FLAGS>(a, x, y, (int)blockIdx.z);
+}
+
+// The non-plain cells of a flagged lattice (solid cells excluded): boundary
+// neighbours, equilibrium and outflow cells, from a list built when the
+// geometry is set, one per thread.
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX, bool CH>
+__global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : 3)
+    k_step_list(const StepArgs<R> a, const uint32_t* __restrict__ cells, uint32_t count) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint32_t n = cells[t];
+    const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
+    const uint32_t z = n / plane, r = n - z * plane;
+    const uint32_t y = r / (uint32_t)a.nx, x = r - y * (uint32_t)a.nx;
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, CH>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- staged kernel
@@ -547,16 +523,9 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
     constexpr uint32_t CHE = (uint32_t)V::Q * CHUNK;     // codes per chunk
     const int lane = threadIdx.x;
     const uint32_t X = blockIdx.x, XT = (uint32_t)a.nx / CHUNK;
-    const int y0 = blockIdx.y * blockDim.y + threadIdx.y;
-    const bool row_ok = y0 < a.ny;                         // the same for a whole warp
-    const int y = row_ok ? y0 : a.ny - 1;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
-    __shared__ uint32_t qcells[PLAIN ? 2 * 256 : 1];
-    __shared__ uint32_t qcount;
-    if constexpr (PLAIN) {
-        if (threadIdx.x == 0 && threadIdx.y == 0) qcount = 0u;
-        __syncthreads();
-    }
+    if (y >= a.ny) return;                                 // whole warps leave together
     const uint32_t ny = (uint32_t)a.ny;
     const uint32_t ry[3] = {(uint32_t)(y == 0 ? a.ny - 1 : y - 1), (uint32_t)y, (uint32_t)(y == a.ny - 1 ? 0 : y + 1)};
     const uint32_t rz[3] = {(uint32_t)(z == 0 ? a.nz - 1 : z - 1) * ny, (uint32_t)z * ny,
@@ -568,18 +537,11 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
     uint16_t* dst = (uint16_t*)a.dst;
     const uint32_t own_chunk = (ry[1] + rz[1]) * XT + X;   // < 2^25: N < 2^31 cells
     uint32_t pl = 3u;   // bit 0: cell 2l is plain, bit 1: cell 2l + 1
-    bool work = row_ok;
     if constexpr (PLAIN) {
-        if (row_ok) {
-            const uint32_t fl2 = reinterpret_cast<const uint16_t*>(a.flags)[own_chunk * (CHUNK / 2) + lane];
-            pl = ((fl2 & 0xFFu) == 0u ? 1u : 0u) | ((fl2 >> 8) == 0u ? 2u : 0u);
-            const uint32_t n0 = own_chunk * CHUNK + 2 * lane;     // cells 2l, 2l + 1 of the chunk
-            if (is_deferred(fl2 & 0xFFu)) CellQueue{qcells, &qcount}.push(n0);
-            if (is_deferred(fl2 >> 8)) CellQueue{qcells, &qcount}.push(n0 + 1);
-            work = __any_sync(0xffffffffu, pl != 0u);      // something plain in this chunk
-        }
+        const uint32_t fl2 = reinterpret_cast<const uint16_t*>(a.flags)[own_chunk * (CHUNK / 2) + lane];
+        pl = ((fl2 & 0xFFu) == 0u ? 1u : 0u) | ((fl2 >> 8) == 0u ? 2u : 0u);
+        if (!__any_sync(0xffffffffu, pl != 0u)) return;   // nothing plain in this chunk
     }
-    if (work) {
     uint32_t g[V::Q];   // lo half: cell 2*lane, hi half: cell 2*lane + 1 (of this chunk)
     if constexpr (PHASE == LAYOUT_AA_NATURAL) {
         const uint32_t* pairs = reinterpret_cast<const uint32_t*>(src + (size_t)own_chunk * CHE) + lane;
@@ -659,12 +621,6 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
             }
         });
     }
-    }   // work
-    if constexpr (PLAIN) {
-        __syncthreads();
-        constexpr int SCH = PHASE == LAYOUT_AB ? SCHEME_AB : (PHASE == LAYOUT_AA_SWAPPED ? SCHEME_AA_PP : SCHEME_AA_LOC);
-        run_queue<V, COLL, FMT, float, SCH, uint32_t, true>(a, qcells, qcount);
-    }
 }
 
 // ---------------------------------------------------------------- ensemble
@@ -685,29 +641,38 @@ template <class R> struct EnsMember {
     FastDiv by_plane, by_nx;
 };
 
-// One launch per step for all members: each block is a tile of one member's
-// consecutive cells; the tile's plain cells take the fast path and its
-// other non-solid cells are deferred to the end of the block (CellQueue).
+// The plain cells (flag byte 0) of every member; the others come from the
+// ensemble's list (k_ensemble_list).
 template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
 __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
-    __shared__ uint32_t qcells[256];
-    __shared__ uint32_t qcount;
-    if (threadIdx.x == 0) qcount = 0u;
-    __syncthreads();
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
     const uint32_t n = (blockIdx.x - M.tile0) * blockDim.x + threadIdx.x;
+    if (n >= M.ncells) return;
     const StepArgs<R> a = M.args[parity];
-    if (n < M.ncells) {
-        const uint32_t z = M.by_plane.div(n);
-        const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
-        const uint32_t y = M.by_nx.div(r);
-        const uint32_t x = r - y * (uint32_t)a.nx;
-        if (is_deferred(a.flags[n])) CellQueue{qcells, &qcount}.push(n);
-        cell_step<V, COLL, FMT, R, SCHEME, true, IX, true>(a, (int)x, (int)y, (int)z);
-    }
-    __syncthreads();
-    run_queue<V, COLL, FMT, R, SCHEME, IX, false>(a, qcells, qcount);
+    const uint32_t z = M.by_plane.div(n);
+    const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
+    const uint32_t y = M.by_nx.div(r);
+    const uint32_t x = r - y * (uint32_t)a.nx;
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, true>(a, (int)x, (int)y, (int)z);
+}
+
+// The non-plain cells of all members: entry = member << 32 | cell.
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
+__global__ void __launch_bounds__(256) k_ensemble_list(const EnsMember<R>* __restrict__ members,
+                                                        const uint64_t* __restrict__ cells, uint32_t count,
+                                                        int parity) {
+    const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    const uint64_t e = cells[t];
+    const EnsMember<R>& M = members[(uint32_t)(e >> 32)];
+    const uint32_t n = (uint32_t)e;
+    const StepArgs<R> a = M.args[parity];
+    const uint32_t z = M.by_plane.div(n);
+    const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
+    const uint32_t y = M.by_nx.div(r);
+    const uint32_t x = r - y * (uint32_t)a.nx;
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- probes

@@ -13,7 +13,11 @@ struct Launch {
 };
 
 using StepFn = cudaError_t (*)(const void* step_args, const Launch&);
+// cells of a flagged lattice from a list (see k_step_list)
+using ListFn = cudaError_t (*)(const void* step_args, const uint32_t* cells, uint32_t count, const Launch&);
 using EnsFn = cudaError_t (*)(const void* members, const uint32_t* tile_member, int parity, const Launch&);
+using EnsListFn = cudaError_t (*)(const void* members, const uint64_t* cells, uint32_t count, int parity,
+                                  const Launch&);
 using ProbeFn = cudaError_t (*)(const void* probe_args, int mode, const Launch&);
 using PutFn = cudaError_t (*)(const void* put_args, int setf, const Launch&);
 // staged flag-free A-B step: grid size, tiles along y, status word
@@ -21,7 +25,10 @@ using StagedFn = cudaError_t (*)(const void* step_args, int grid, int tiles_y, i
 
 struct KernelSet {
     StepFn step[3][2][2] = {};   // [scheme: AB, AA_PP, AA_LOC][flags][32-bit indices]
-    EnsFn ens[3][2] = {};        // [scheme][32-bit indices], flags always on
+    ListFn list[3][2] = {};      // [scheme][32-bit indices]: the non-plain cells of a flagged lattice
+    ListFn list_chunked[3] = {}; // [scheme]: the same on the chunked layout
+    EnsFn ens[3][2] = {};        // [scheme][32-bit indices], flags always on: plain cells
+    EnsListFn ens_list[3][2] = {};   // the listed non-plain cells of all members
     ProbeFn probe[8] = {};    // [layout code: phase | 4 if chunked]
     PutFn put[4] = {};        // [bit 0: A-A, bit 1: chunked]
     StagedFn staged[3] = {};  // row length 128, 256, 512 (D3Q19, FP32 arithmetic only)
