@@ -324,14 +324,46 @@ template <> struct Storage<0> {   // FP64
     template <class R, class IX> __device__ static R load_g(const T* p, IX i) { return (R)p[i]; }
     template <class R, class IX> __device__ static void store_g(T* p, IX i, R v) { p[i] = (double)v; }
 };
+// FP32 <-> FP64 on the integer pipe.  On GB300 the FP64 pipe bounds the
+// FP64-arithmetic tiers, and the hardware conversions run there too, so the
+// FP64/FP32 tier converts in integer arithmetic (IEEE 754 binary32 and
+// binary64 encodings; round to nearest even).  Zeros are handled here; the
+// rare cases outside the normal range of the result go to the hardware.
+__device__ __forceinline__ double f32_to_f64(float x) {
+    const uint32_t b = __float_as_uint(x);
+    const uint32_t mag = b & 0x7FFFFFFFu;
+    if (mag == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+    if ((mag >> 23) - 1u >= 254u) return (double)x;   // subnormal, Inf, NaN
+    // exponent + (1023 - 127) in the high word, mantissa split across both words
+    const uint32_t hi = (b & 0x80000000u) | ((mag >> 3) + 0x38000000u);
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+__device__ __forceinline__ float f64_to_f32(double v) {
+    const uint32_t hi = (uint32_t)__double2hiint(v), lo = (uint32_t)__double2loint(v);
+    const uint32_t e = (hi >> 20) & 0x7FFu;
+    if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
+    if (e - 897u >= 254u) return (float)v;            // result subnormal, zero, huge, Inf or NaN
+    // 23-bit mantissa and exponent - (1023 - 127), from the upper word of (hi:lo) << 3
+    const uint32_t m = __funnelshift_l(lo, hi, 3) - 0x1C000000u;
+    const uint32_t rem = lo & 0x1FFFFFFFu;          // the 29 dropped bits
+    const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
+    return __uint_as_float((hi & 0x80000000u) | (m + up));
+}
+template <class R> __device__ __forceinline__ R from_f32(float x) {
+    if constexpr (sizeof(R) == 8) return f32_to_f64(x); else return x;
+}
+template <class R> __device__ __forceinline__ float to_f32(R v) {
+    if constexpr (sizeof(R) == 8) return f64_to_f32(v); else return v;
+}
+
 template <> struct Storage<1> {   // FP32
     using T = float;
     static constexpr int bytes = 4;
     static constexpr int SL = 0;
-    template <class R, class IX> __device__ static R load(const T* p, IX i) { return (R)p[i]; }
-    template <class R, class IX> __device__ static void store(T* p, IX i, R v) { p[i] = (float)v; }
-    template <class R, class IX> __device__ static R load_g(const T* p, IX i) { return (R)p[i]; }
-    template <class R, class IX> __device__ static void store_g(T* p, IX i, R v) { p[i] = (float)v; }
+    template <class R, class IX> __device__ static R load(const T* p, IX i) { return from_f32<R>(p[i]); }
+    template <class R, class IX> __device__ static void store(T* p, IX i, R v) { p[i] = to_f32(v); }
+    template <class R, class IX> __device__ static R load_g(const T* p, IX i) { return from_f32<R>(p[i]); }
+    template <class R, class IX> __device__ static void store_g(T* p, IX i, R v) { p[i] = to_f32(v); }
 };
 
 // ---------------------------------------------------------------- collision

@@ -205,7 +205,8 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     constexpr int PH = SCHEME == SCHEME_AB ? LAYOUT_AB
                      : (SCHEME == SCHEME_AA_PP ? LAYOUT_AA_SWAPPED : LAYOUT_AA_NATURAL);
     constexpr int LAYOUT = PH | (CH ? LAYOUT_CHUNKED : 0);
-    const uint32_t fl = FLAGS ? (uint32_t)a.flags[n] : 0u;
+    // PLAIN_ONLY reads the flag byte too, but compiles no boundary code
+    const uint32_t fl = (FLAGS || PLAIN_ONLY) ? (uint32_t)a.flags[n] : 0u;
     // The plain pull is issued for every cell together with the flag load,
     // so the two memory latencies overlap; solid and equilibrium cells drop
     // it, cells next to solid cells gather again with their boundaries.
@@ -250,11 +251,13 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
 // FLAGS: the lattice has flags; then this kernel updates the plain cells
 // (flag byte 0) only and k_step_list the listed others.
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
-__global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8) ? 2 : (FLAGS ? 3 : 4)) k_step(const StepArgs<R> a) {
+__global__ void __launch_bounds__(256, (sizeof(R) == 8 || (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8)) ? 2 : 4)
+    k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
-    cell_step<V, COLL, FMT, R, SCHEME, FLAGS, IX, FLAGS>(a, x, y, (int)blockIdx.z);
+    // with flags: the flag-free update of the plain cells only (no boundary code)
+    cell_step<V, COLL, FMT, R, SCHEME, false, IX, FLAGS>(a, x, y, (int)blockIdx.z);
 }
 
 // The non-plain cells of a flagged lattice (solid cells excluded): boundary
@@ -644,7 +647,7 @@ template <class R> struct EnsMember {
 // The plain cells (flag byte 0) of every member; the others come from the
 // ensemble's list (k_ensemble_list).
 template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
-__global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __restrict__ members,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
     const uint32_t n = (blockIdx.x - M.tile0) * blockDim.x + threadIdx.x;
@@ -654,7 +657,7 @@ __global__ void __launch_bounds__(256) k_ensemble_step(const EnsMember<R>* __res
     const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
     const uint32_t y = M.by_nx.div(r);
     const uint32_t x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, true, IX, true>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, false, IX, true>(a, (int)x, (int)y, (int)z);
 }
 
 // The non-plain cells of all members: entry = member << 32 | cell.
