@@ -242,6 +242,14 @@ lbm_status lbm_set_variant(lbm_handle* h, int variant);
  * _PAIRED), or -1 for a NULL handle. */
 int lbm_get_variant(const lbm_handle* h);
 
+/* Switch the streaming scheme of a live lattice (LBM_STREAM_AB or _AA)
+ * without changing a value: after an even number of steps the A-B state
+ * and the A-A state differ only by a swap of opposite slots.  AB -> AA
+ * releases the second population copy (half the memory); AA -> AB
+ * allocates it.  Errors: LBM_ERR_STATE after an odd number of steps,
+ * LBM_ERR_UNSUPPORTED for A-A with OUTFLOW or FREESLIP cells, LBM_ERR_OOM. */
+lbm_status lbm_set_scheme(lbm_handle* h, int scheme);
+
 /* Same search as lbm_ensemble_autotune for one lattice; the trial steps
  * advance the lattice. */
 lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx, int* by);
@@ -287,11 +295,16 @@ lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps);
 /* Cells per tile (thread block) of the ensemble launch: bx a multiple of 32
  * in [32, 256], by must be 1 (tiles are runs of consecutive cells). */
 lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by);
-/* Times trial_steps steps for each of a fixed list of tile sizes and keeps
- * the fastest.  The trial steps are real steps: every member advances by
- * (trial_steps + 2) * (number of shapes) steps.  Results do not depend on
- * the tile shape. */
+/* Picks the tile size and the streaming scheme: times trial_steps steps
+ * (rounded up to even) for each of a fixed list of tile sizes, then, where
+ * every member allows it (A-A: no OUTFLOW or FREESLIP cells; memory for the
+ * A-B copies) and the step count is even, converts all members to the other
+ * scheme (lbm_set_scheme) and times again; keeps the fastest combination.
+ * The trial steps are real steps (two warm-up steps per tile size on top).
+ * Results do not depend on the tile size or the scheme. */
 lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx, int* by);
+/* The streaming scheme the ensemble's members use now (-1 for NULL). */
+int lbm_ensemble_scheme(const lbm_ensemble* e);
 lbm_status lbm_ensemble_destroy(lbm_ensemble* e);
 const char* lbm_ensemble_last_error(const lbm_ensemble* e);
 

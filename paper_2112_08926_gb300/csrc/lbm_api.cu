@@ -278,6 +278,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
     if (st != LBM_OK) return st;
     const size_t N = h->N;
     if (!flags) {
+        h->has_open_boundaries = false;
         h->release((void*&)h->special, (size_t)h->special_cap * sizeof(uint32_t));
         h->special_cap = 0;
         h->n_special = 0;
@@ -286,7 +287,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         h->release((void*&)h->node_rho, N * sizeof(float));
         return ensure_layout(h);
     }
-    bool any_moving = false, any_eq = false;
+    bool any_moving = false, any_eq = false, any_open = false;
     for (size_t n = 0; n < N; ++n) {
         const uint32_t fl = flags[n];
         const bool wall = fl & LBM_WALL;
@@ -305,6 +306,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         if (h->aa() && (fl & (LBM_OUTFLOW | LBM_FREESLIP)))
             return h->fail(LBM_ERR_UNSUPPORTED, "A-A streaming supports no OUTFLOW or FREESLIP cells");
         any_moving |= (fl & LBM_MOVING) != 0;
+        any_open |= (fl & (LBM_OUTFLOW | LBM_FREESLIP)) != 0;
         any_eq |= (fl & LBM_EQ) != 0;
     }
     if (!h->flags) {
@@ -313,6 +315,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
     }
     if (h->cuda(cudaMemcpyAsync(h->flags, flags, N, cudaMemcpyHostToDevice, h->stream), "flags upload"))
         return LBM_ERR_CUDA;
+    h->has_open_boundaries = any_open;
     const bool need_u = node_u || any_moving || any_eq;
     const bool need_rho = node_rho || any_eq;
     if (need_u && !h->node_u) {
@@ -928,6 +931,62 @@ extern "C" lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx_out, 
     if (bx_out) *bx_out = bb[0];
     if (by_out) *by_out = bb[1];
     return st;
+}
+
+namespace {
+
+// swaps slots p and p+1 (odd p: opposite directions) of every cell, in the
+// SoA or the chunked layout; the rest slot stays
+template <class T>
+__global__ void k_swap_slots(T* f, int q, uint32_t N, int chunked) {
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+        for (int p = 1; p < q; p += 2) {
+            const size_t a = chunked ? ((size_t)(n >> 6) * q + p) * lbm::CHUNK + (n & (lbm::CHUNK - 1))
+                                     : (size_t)p * N + n;
+            const size_t b = chunked ? a + lbm::CHUNK : a + N;
+            const T t = f[a];
+            f[a] = f[b];
+            f[b] = t;
+        }
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_set_scheme(lbm_handle* h, int scheme) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    if (scheme != LBM_STREAM_AB && scheme != LBM_STREAM_AA) return h->fail(LBM_ERR_ARG, "scheme");
+    if (scheme == h->p.scheme) return LBM_OK;
+    if (h->t & 1) return h->fail(LBM_ERR_STATE, "the streaming scheme can change after an even number of steps only");
+    if (scheme == LBM_STREAM_AA && h->has_open_boundaries)
+        return h->fail(LBM_ERR_UNSUPPORTED, "A-A streaming supports no OUTFLOW or FREESLIP cells");
+    const size_t fbytes = (size_t)h->q * h->N * h->sb;
+    if (scheme == LBM_STREAM_AB) {   // a second copy first: failing leaves the lattice as it was
+        void* other = h->alloc(fbytes);
+        if (!other) return h->fail(LBM_ERR_OOM, "second population copy");
+        h->f[1] = other;
+    }
+    void* live = scheme == LBM_STREAM_AA ? h->f[h->cur] : h->f[0];
+    // A-B after an even step count: slot i of cell x holds what x streams out
+    // along i; A-A before its odd half holds the same value in slot opposite(i)
+    const unsigned grid = (unsigned)std::min<size_t>((h->N + 255) / 256, 152 * 32);
+    const int ch = h->chunked;
+    if (h->sb == 8) k_swap_slots<double><<<grid, 256, 0, h->stream>>>((double*)live, h->q, (uint32_t)h->N, ch);
+    else if (h->sb == 4) k_swap_slots<float><<<grid, 256, 0, h->stream>>>((float*)live, h->q, (uint32_t)h->N, ch);
+    else k_swap_slots<uint16_t><<<grid, 256, 0, h->stream>>>((uint16_t*)live, h->q, (uint32_t)h->N, ch);
+    if (h->cuda(cudaGetLastError(), "swap kernel")) return LBM_ERR_CUDA;
+    if (scheme == LBM_STREAM_AA) {
+        void* spare = h->f[1 - h->cur];
+        h->f[0] = live;
+        h->f[1] = nullptr;
+        h->release(spare, fbytes);   // stream-ordered: the swap kernel does not touch it
+    } else {
+        // the copy the next step writes must hold zero populations for solid cells
+        if (h->cuda(cudaMemsetAsync(h->f[1], 0, fbytes, h->stream), "memset")) return LBM_ERR_CUDA;
+    }
+    h->cur = 0;
+    h->p.scheme = scheme;
+    return ensure_layout(h);
 }
 
 extern "C" lbm_status lbm_set_variant(lbm_handle* h, int variant) {

@@ -343,8 +343,9 @@ __device__ __forceinline__ float f64_to_f32(double v) {
     const uint32_t e = (hi >> 20) & 0x7FFu;
     if (((hi & 0x7FFFFFFFu) | lo) == 0u) return __uint_as_float(hi & 0x80000000u);
     if (e - 897u >= 254u) return (float)v;            // result subnormal, zero, huge, Inf or NaN
-    // 23-bit mantissa and exponent - (1023 - 127), from the upper word of (hi:lo) << 3
-    const uint32_t m = __funnelshift_l(lo, hi, 3) - 0x1C000000u;
+    // 23-bit mantissa and exponent - (1023 - 127): the upper word of (hi:lo) << 3
+    // minus 896 << 23 (mod 2^32; the exponent's bits above bit 31 cancel)
+    const uint32_t m = __funnelshift_l(lo, hi, 3) - 0xC0000000u;
     const uint32_t rem = lo & 0x1FFFFFFFu;          // the 29 dropped bits
     const uint32_t up = (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) ? 1u : 0u;
     return __uint_as_float((hi & 0x80000000u) | (m + up));

@@ -296,16 +296,17 @@ extern "C" lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by) {
     return upload_table(e);
 }
 
-extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx_out, int* by_out) {
-    if (!e || trial_steps < 1) return LBM_ERR_ARG;
-    static const int shapes[][2] = {{256, 1}, {128, 1}, {64, 1}, {192, 1}, {96, 1}};
-    float best = INFINITY;
-    int bb[2] = {e->tile, 1};
+namespace {
+
+// times every tile size for the current scheme; returns the best (ms, tile)
+lbm_status time_tiles(lbm_ensemble* e, int trial_steps, float* best_ms, int* best_tile) {
+    static const int tiles[] = {256, 128, 64, 192, 96};
     cudaEvent_t ev[2];
     if (e->cuda(cudaEventCreate(&ev[0]), "event") || e->cuda(cudaEventCreate(&ev[1]), "event")) return LBM_ERR_CUDA;
     lbm_status st = LBM_OK;
-    for (const auto& sh : shapes) {
-        st = lbm_ensemble_set_block(e, sh[0], sh[1]);
+    *best_ms = INFINITY;
+    for (int tile : tiles) {
+        st = lbm_ensemble_set_block(e, tile, 1);
         if (st != LBM_OK) break;
         st = lbm_ensemble_step(e, 2);   // warm-up
         if (st != LBM_OK) break;
@@ -316,15 +317,67 @@ extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, in
         if (e->cuda(cudaEventSynchronize(ev[1]), "event sync")) { st = LBM_ERR_CUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (ms < best) { best = ms; bb[0] = sh[0]; bb[1] = sh[1]; }
+        if (ms < *best_ms) { *best_ms = ms; *best_tile = tile; }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
-    if (st != LBM_OK) return st;
-    st = lbm_ensemble_set_block(e, bb[0], bb[1]);
-    if (bx_out) *bx_out = bb[0];
-    if (by_out) *by_out = bb[1];
     return st;
+}
+
+// converts every member (lbm_set_scheme) and rebuilds the ensemble's tables
+lbm_status switch_scheme(lbm_ensemble* e, int scheme) {
+    const int back = e->aa ? LBM_STREAM_AA : LBM_STREAM_AB;
+    for (size_t k = 0; k < e->m.size(); ++k) {
+        const lbm_status st = lbm_set_scheme(e->m[k], scheme);
+        if (st != LBM_OK) {   // e.g. no memory for A-B copies: undo the members switched so far
+            e->err = std::string("scheme switch: ") + lbm_last_error(e->m[k]);
+            for (size_t j = 0; j < k; ++j) lbm_set_scheme(e->m[j], back);
+            return st;
+        }
+    }
+    e->aa = scheme == LBM_STREAM_AA;
+    for (lbm_handle* h : e->m) e->idx32 = e->idx32 && h->idx32();
+    return upload_table(e);
+}
+
+bool can_use_aa(const lbm_ensemble* e) {
+    for (const lbm_handle* h : e->m)
+        if (h->has_open_boundaries) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx_out, int* by_out) {
+    if (!e || trial_steps < 1) return LBM_ERR_ARG;
+    lbm_status st = check_members(e);
+    if (st != LBM_OK) return st;
+    trial_steps += trial_steps & 1;       // whole A-A step pairs: the scheme may change between trials
+    float ms0 = 0.f, ms1 = INFINITY;
+    int tile0 = e->tile, tile1 = e->tile;
+    st = time_tiles(e, trial_steps, &ms0, &tile0);
+    if (st != LBM_OK) return st;
+    const int scheme0 = e->aa ? LBM_STREAM_AA : LBM_STREAM_AB;
+    const int scheme1 = e->aa ? LBM_STREAM_AB : LBM_STREAM_AA;
+    // the other streaming scheme, where every member allows it (A-A: no
+    // outflow or free-slip cells) and the memory for A-B copies is there
+    bool other = (scheme1 == LBM_STREAM_AB || can_use_aa(e)) && ((e->t0[0] + e->s) & 1) == 0;
+    if (other && switch_scheme(e, scheme1) == LBM_OK) {
+        st = time_tiles(e, trial_steps, &ms1, &tile1);
+        if (st != LBM_OK) return st;
+        if (ms0 <= ms1 && (st = switch_scheme(e, scheme0)) != LBM_OK) return st;
+    } else {
+        other = false;
+    }
+    const int tile = other && ms1 < ms0 ? tile1 : tile0;
+    st = lbm_ensemble_set_block(e, tile, 1);
+    if (bx_out) *bx_out = tile;
+    if (by_out) *by_out = 1;
+    return st;
+}
+
+extern "C" int lbm_ensemble_scheme(const lbm_ensemble* e) {
+    return e ? (e->aa ? LBM_STREAM_AA : LBM_STREAM_AB) : -1;
 }
 
 extern "C" const char* lbm_ensemble_last_error(const lbm_ensemble* e) { return e ? e->err.c_str() : "null ensemble"; }

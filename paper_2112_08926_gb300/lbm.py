@@ -42,6 +42,7 @@ EXPORTS = [
     "lbm_ensemble_set_block", "lbm_ensemble_autotune", "lbm_ensemble_destroy",
     "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant", "lbm_get_rho_u_static",
     "lbm_set_nodes", "lbm_get_f_cells", "lbm_get_rho_u_cells", "lbm_selftest_wait_timeout",
+    "lbm_set_scheme", "lbm_ensemble_scheme",
 ]
 
 
@@ -106,6 +107,8 @@ def load() -> ctypes.CDLL:
             "lbm_get_f": [P, P],
             "lbm_set_nodes": [P, I64, P, P, P],
             "lbm_selftest_wait_timeout": [P],
+            "lbm_set_scheme": [P, I],
+            "lbm_ensemble_scheme": [P],
             "lbm_get_f_cells": [P, I64, P, P],
             "lbm_get_rho_u_cells": [P, I64, P, P, P, P, P],
             "lbm_set_f": [P, P],
@@ -340,6 +343,11 @@ class Lattice:
         self._c(self._L.lbm_autotune(self._h, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)))
         return bx.value, by.value
 
+    def set_scheme(self, scheme: str):
+        """Switch between A-B and in-place A-A streaming (after an even step count)."""
+        self._c(self._L.lbm_set_scheme(self._h, SCHEMES[scheme]))
+        self.scheme = scheme
+
     def set_variant(self, variant: str):
         """'auto', 'generic', 'staged' or 'paired' (see lbm_set_variant)."""
         self._c(self._L.lbm_set_variant(self._h, VARIANTS[variant]))
@@ -380,10 +388,14 @@ class Ensemble:
         _check(self._L.lbm_ensemble_set_block(self._e, int(bx), int(by)), self._e, ensemble=True)
 
     def autotune(self, trial_steps=5):
+        """Picks tile size and streaming scheme; returns (tile, 1)."""
         bx, by = ctypes.c_int(), ctypes.c_int()
         _check(self._L.lbm_ensemble_autotune(self._e, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)),
                self._e, ensemble=True)
         return bx.value, by.value
+
+    def scheme(self) -> str:
+        return {v: k for k, v in SCHEMES.items()}[self._L.lbm_ensemble_scheme(self._e)]
 
 
 # ---------------------------------------------------------------- codecs

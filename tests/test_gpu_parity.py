@@ -412,3 +412,55 @@ def test_d3q27_stays_generic():
     g.set_variant("paired")
     assert g.variant() == "generic" and g.info().layout == 0
     g.close()
+
+
+@pytest.mark.parametrize("storage,shape", [("FP16S", (3, 7, 128)), ("FP32", (5, 9, 37)), ("P16_1S", (4, 6, 64))])
+def test_scheme_switch_keeps_values(storage, shape):
+    """lbm_set_scheme: A-B <-> in-place A-A on a live lattice (even step counts)."""
+    nz, ny, nx = shape
+    geo = W.random_geometry(shape, 61, outflow=0.0, freeslip_frac=0.0)
+    fields = W.random_fields(shape, 62)
+    g = P().Lattice(nx, ny, nz, "D3Q19", "TRT", storage, "FP32", "AB", tau=0.7)
+    g.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "TRT", "ORD32", storage, tau=0.7)
+    o.set_geometry(*geo)
+    o.set_rho_u(*fields)
+    g.step(10)
+    mem_ab = g.info().device_bytes
+    g.set_scheme("AA")
+    assert g.info().device_bytes < mem_ab
+    g.step(11)
+    with pytest.raises(P().LBMError) as e:      # odd step count
+        g.set_scheme("AB")
+    assert e.value.status == 7
+    g.step(1)
+    g.set_scheme("AB")
+    g.step(3)
+    o.step(25)
+    assert np.array_equal(g.f(), o.f())
+    g.close()
+
+
+def test_ensemble_autotune_picks_scheme_bitwise():
+    specs = W.ensemble_cavities(count=6, n_min=6, n_max=19, seed=5)
+    def members():
+        out = []
+        for s in specs:
+            g = P().Lattice(s.n, s.n, s.n, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=s.tau)
+            g.set_geometry(W.cavity_flags(s.n))
+            g.set_nodes(*W.cavity_lid(s.n, s.u_lid))
+            g.set_rho_u()
+            out.append(g)
+        return out
+    a, b = members(), members()
+    e = P().Ensemble(a)
+    e.autotune(trial_steps=3)
+    assert e.scheme() in ("AB", "AA")
+    done = a[0].info().step
+    e.step(40 - done)
+    for g in b:
+        g.step(40)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
+    e.close()
