@@ -214,3 +214,54 @@ def test_taylor_green_2d_plateau_without_shifting():
     for storage in ("P16_1S", "P16_2C"):
         ps, pu = res[storage]
         assert pu == 0.0 or pu > 10 * ps, storage
+
+
+def cylinder_poiseuille_error(P, arith, storage, R, u_max=0.1, re=10.0, shifting=True, diffusion_times=12):
+    """Sec. 4.1: D3Q19 SRT flow through a cylinder of radius R driven by the
+    Guo force f = 4 rho nu u_max / R^2, nu = 2 R u_max / Re; relative L2 error
+    of u_x over the fluid cells against u_theo(r) = f (R^2 - r^2) / (4 rho nu)
+    once the flow has settled (diffusion_times * R^2 / nu steps)."""
+    flags, r = W.cylinder_channel(R)
+    nu = 2 * R * u_max / re
+    tau = 3 * nu + 0.5
+    f = 4 * nu * u_max / R ** 2
+    L = flags.shape[0]
+    g = P.Lattice(1, L, L, "D3Q19", "SRT", storage, arith, "AB", tau=tau, force=(f, 0, 0), shifting=shifting)
+    g.set_geometry(flags)
+    g.set_rho_u()
+    g.step(int(diffusion_times * R * R / nu))
+    ux = g.rho_u()[1]
+    g.close()
+    fluid = flags == 0
+    theo = f * (R * R - r * r) / (4 * nu)
+    return float(np.sqrt(np.sum((ux - theo)[fluid] ** 2) / np.sum(theo[fluid] ** 2)))
+
+
+def test_cylinder_poiseuille_radius_sweep():
+    """Sec. 4.1 radius sweep at Re = 10, u_max = 0.1 (with and without DDF
+    shifting): every tier matches FP64 where the staircase of the wall
+    dominates (small R); FP32 stays with FP64 at every R; FP16 and FP16S
+    fall behind at large R; without shifting the 16-bit tiers fail."""
+    P = _pkg()
+    radii = [7, 15, 31, 63]
+    tiers = [("FP64", "FP64"), ("FP32", "FP32"), ("FP32", "FP16"), ("FP32", "FP16S"), ("FP32", "FP16C"),
+             ("FP32", "P16_1S"), ("FP32", "P16_2C")]
+    err, err_ns = {}, {}
+    for arith, storage in tiers:
+        for R in radii:
+            err[(storage, R)] = cylinder_poiseuille_error(P, arith, storage, R)
+            if storage != "FP64":
+                err_ns[(storage, R)] = cylinder_poiseuille_error(P, arith, storage, R, shifting=False)
+    lines = ["tier          " + "".join(f"R={R:<4d}     " for R in radii)]
+    for arith, storage in tiers:
+        lines.append(f"{arith}/{storage:7s}" + "".join(f"{err[(storage, R)]:.3e}  " for R in radii))
+        if storage != "FP64":
+            lines.append(f"  unshifted   " + "".join(f"{err_ns[(storage, R)]:.3e}  " for R in radii))
+    print("\nCylinder Poiseuille, D3Q19 SRT, Re=10, u_max=0.1: relative L2 error of u_x\n" + "\n".join(lines))
+    for R in radii:
+        assert abs(err[("FP32", R)] / err[("FP64", R)] - 1) < 0.1
+    for storage in ("FP16", "FP16S", "FP16C", "P16_1S", "P16_2C"):
+        assert err[(storage, 7)] < 1.5 * err[("FP64", 7)], storage
+    assert err[("FP16", 63)] > 2 * err[("FP64", 63)] and err[("FP16S", 63)] > 2 * err[("FP64", 63)]
+    for storage in ("FP16", "FP16S", "FP16C"):
+        assert err_ns[(storage, 63)] > 10 * err[(storage, 63)], storage

@@ -211,3 +211,15 @@ def ensemble_cavities(count=512, seed=20211216, n_min=16, n_max=128,
         u = u_range[0] + (c >> 11) * (1.0 / (1 << 53)) * (u_range[1] - u_range[0])
         out.append(CavitySpec(int(n), float(tau), float(u)))
     return out
+
+
+def cylinder_channel(R):
+    """Sec. 4.1 channel: L_x = 1, L_y = L_z = 2 (R + 1), axis along x through
+    the box centre; a cell is solid when its centre lies outside radius R.
+    Returns (flags (nz, ny, 1), r of every cell centre (nz, ny, 1))."""
+    L = 2 * (R + 1)
+    c = np.arange(L) + 0.5 - L / 2.0
+    z, y = np.meshgrid(c, c, indexing="ij")
+    r = np.sqrt(y * y + z * z)[:, :, None]
+    flags = np.where(r > R, WALL, 0).astype(np.uint8)
+    return flags, r
