@@ -195,7 +195,7 @@ __device__ __forceinline__ uint32_t gather(const StepArgs<R>& a, const typename 
 // equilibrium neighbour -- are updated; the others are left to the list
 // kernel, so no warp runs the boundary path for a few of its lanes.
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX, bool PLAIN_ONLY = false,
-          bool CH = false>
+          bool CH = false, bool SPEC = true>
 __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, int z) {
     using S = Storage<FMT>;
     using T = typename S::T;
@@ -207,19 +207,22 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     constexpr int LAYOUT = PH | (CH ? LAYOUT_CHUNKED : 0);
     // PLAIN_ONLY reads the flag byte too, but compiles no boundary code
     const uint32_t fl = (FLAGS || PLAIN_ONLY) ? (uint32_t)a.flags[n] : 0u;
-    // The plain pull is issued for every cell together with the flag load,
-    // so the two memory latencies overlap; solid and equilibrium cells drop
-    // it, cells next to solid cells gather again with their boundaries.
+    // SPEC: the plain pull is issued for every cell together with the flag
+    // load, so the two memory latencies overlap; solid and equilibrium cells
+    // drop it, cells next to solid cells gather again with their boundaries.
+    // Without SPEC (cells known to be boundary cells) each cell gathers once.
     R f[V::Q];
     uint32_t walls = 0;   // directions with a solid upstream (= downstream of the opposite) cell
-    gather<V, FMT, R, false, LAYOUT, IX>(a, src, x, y, z, n, 0u, f);
+    if constexpr (SPEC) gather<V, FMT, R, false, LAYOUT, IX>(a, src, x, y, z, n, 0u, f);
     if (PLAIN_ONLY && fl != 0u) return;
     if (FLAGS && (fl & F_WALL)) return;
     if (FLAGS && (fl & F_EQ)) {
         const R u[3] = {(R)a.node_u[n], (R)a.node_u[(size_t)a.N + n], (R)a.node_u[2 * (size_t)a.N + n]};
         equilibrium_only<V, R, S::SL>((R)a.node_rho[n], u, f, a.k.sh);
     } else {
-        if (FLAGS && (fl & (PH == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
+        if constexpr (!SPEC)
+            walls = gather<V, FMT, R, FLAGS, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
+        else if (FLAGS && (fl & (PH == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
             walls = gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
         collide<V, COLL, R, S::SL>(a.k, f);
     }
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(256, (SCHEME == SCHEME_AA_PP && sizeof(IX) == 
     const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
     const uint32_t z = n / plane, r = n - z * plane;
     const uint32_t y = r / (uint32_t)a.nx, x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, CH>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, CH, false>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- staged kernel
@@ -675,7 +678,7 @@ __global__ void __launch_bounds__(256) k_ensemble_list(const EnsMember<R>* __res
     const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
     const uint32_t y = M.by_nx.div(r);
     const uint32_t x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, true, IX>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, false, false>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- probes

@@ -241,7 +241,8 @@ def test_cylinder_poiseuille_radius_sweep():
     """Sec. 4.1 radius sweep at Re = 10, u_max = 0.1 (with and without DDF
     shifting): every tier matches FP64 where the staircase of the wall
     dominates (small R); FP32 stays with FP64 at every R; FP16 and FP16S
-    fall behind at large R; without shifting the 16-bit tiers fail."""
+    fall behind at large R, FP16C later, the scaled posits hold up best;
+    without shifting the 16-bit tiers fail."""
     P = _pkg()
     radii = [7, 15, 31, 63]
     tiers = [("FP64", "FP64"), ("FP32", "FP32"), ("FP32", "FP16"), ("FP32", "FP16S"), ("FP32", "FP16C"),
@@ -263,5 +264,7 @@ def test_cylinder_poiseuille_radius_sweep():
     for storage in ("FP16", "FP16S", "FP16C", "P16_1S", "P16_2C"):
         assert err[(storage, 7)] < 1.5 * err[("FP64", 7)], storage
     assert err[("FP16", 63)] > 2 * err[("FP64", 63)] and err[("FP16S", 63)] > 2 * err[("FP64", 63)]
-    for storage in ("FP16", "FP16S", "FP16C"):
-        assert err_ns[(storage, 63)] > 10 * err[(storage, 63)], storage
+    # the posits hold up best at large R (their accurate interval fits the populations)
+    assert err[("P16_1S", 63)] < 1.5 * err[("FP64", 63)]
+    for storage in ("FP16", "FP16S", "FP16C", "P16_1S", "P16_2C"):
+        assert err_ns[(storage, 63)] > 5 * err[(storage, 63)], storage
