@@ -29,7 +29,7 @@ FORMATS = {
 }
 CODEC_FORMATS = ["FP16", "FP16S", "FP16C", "P16_0S", "P16_1S", "P16_2C", "P16_0", "P16_1"]
 VELSETS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISIONS = {"SRT": 0, "TRT": 1}
+COLLISIONS = {"SRT": 0, "TRT": 1, "MRT": 2}
 ARITH = {"DEF64": 0, "ORD32": 1, "ORD64": 2}
 
 WALL, MOVING, EQ, OUTFLOW, FREESLIP = 0x01, 0x02, 0x04, 0x08, 0x10
@@ -82,6 +82,8 @@ def lib() -> ctypes.CDLL:
             L.orc_encode_bits_range.argtypes = [ctypes.c_int, ctypes.c_uint32, i64, P]
             L.orc_velset_q.argtypes = [ctypes.c_int]
             L.orc_velset_table.argtypes = [ctypes.c_int, P, P]
+            L.orc_mrt_basis.argtypes = [P]
+            L.orc_mrt_rates.argtypes = [ctypes.c_double, P]
             L.orc_create.restype = P
             L.orc_create.argtypes = [ctypes.POINTER(_Params)]
             L.orc_destroy.argtypes = [P]
@@ -138,6 +140,19 @@ def equilibrium(vs: str, arith: str, rho: float, u) -> np.ndarray:
     out = np.zeros(q, dtype=np.float64)
     lib().orc_equilibrium(VELSETS[vs], ARITH[arith], float(rho), float(u[0]), float(u[1]),
                           float(u[2]) if len(u) > 2 else 0.0, _ptr(out))
+    return out
+
+
+def mrt_basis() -> np.ndarray:
+    """The D3Q19 MRT moment basis (19 x 19) the oracle uses."""
+    out = np.zeros((19, 19), dtype=np.float64)
+    lib().orc_mrt_basis(_ptr(out))
+    return out
+
+
+def mrt_rates(tau: float) -> np.ndarray:
+    out = np.zeros(19, dtype=np.float64)
+    lib().orc_mrt_rates(ctypes.c_double(tau), _ptr(out))
     return out
 
 

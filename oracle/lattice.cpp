@@ -85,6 +85,45 @@ inline int opp(int i) { return i == 0 ? 0 : ((i & 1) ? i + 1 : i - 1); }
 
 inline int wrap(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
+/* D3Q19 multiple-relaxation-time basis of d'Humieres et al. (2002), the MRT
+ * operator the paper's roofline (Sec. 5) lists next to SRT and TRT without
+ * defining it.  Rows (moments of the populations): rho, e, epsilon, j_x,
+ * q_x, j_y, q_y, j_z, q_z, 3 p_xx, 3 pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz,
+ * m_x, m_y, m_z, as polynomials of the lattice velocity c (|c|^2 = c.c). */
+double mrt_entry(int k, const int* c) {
+    const double x = c[0], y = c[1], z = c[2], c2 = x * x + y * y + z * z;
+    switch (k) {
+    case 0: return 1.0;
+    case 1: return 19.0 * c2 - 30.0;
+    case 2: return (21.0 * c2 * c2 - 53.0 * c2 + 24.0) / 2.0;
+    case 3: return x;
+    case 4: return (5.0 * c2 - 9.0) * x;
+    case 5: return y;
+    case 6: return (5.0 * c2 - 9.0) * y;
+    case 7: return z;
+    case 8: return (5.0 * c2 - 9.0) * z;
+    case 9: return 3.0 * x * x - c2;
+    case 10: return (3.0 * c2 - 5.0) * (3.0 * x * x - c2);
+    case 11: return y * y - z * z;
+    case 12: return (3.0 * c2 - 5.0) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return x * (y * y - z * z);
+    case 17: return y * (z * z - x * x);
+    default: return z * (x * x - y * y);
+    }
+}
+/* relaxation rates of d'Humieres et al. (2002): the shear moments relax with
+ * omega = 1/tau (they set the viscosity), the conserved ones too (their
+ * non-equilibrium part is the Guo half force only), the others with fixed
+ * rates */
+void mrt_rates(double tau, double* s) {
+    const double om = 1.0 / tau;
+    const double fixed[19] = {om, 1.19, 1.4, om, 1.2, om, 1.2, om, 1.2, om, 1.4, om, 1.4, om, om, om, 1.98, 1.98, 1.98};
+    for (int k = 0; k < 19; ++k) s[k] = fixed[k];
+}
+
 inline double fmaR(double a, double b, double c) { return std::fma(a, b, c); }
 inline float fmaR(float a, float b, float c) { return std::fmaf(a, b, c); }
 
@@ -148,6 +187,50 @@ struct Ordered {
         for (int a = 0; a < 3; ++a) F[a] = (R)L->p.force[a];
         force = L->has_force();
         sh = L->p.no_shift ? (R)0 : (R)1;
+        if (L->p.collision == ORC_MRT) {
+            double s[19];
+            mrt_rates(L->p.tau, s);
+            for (int k = 0; k < 19; ++k) {
+                double norm = 0.0;
+                for (int i = 0; i < 19; ++i) {
+                    Mk[k][i] = mrt_entry(k, vs.c[i]);
+                    norm += Mk[k][i] * Mk[k][i];
+                }
+                rk[k] = (R)(s[k] / norm);
+                pk[k] = (R)((1.0 - 0.5 * s[k]) / norm);
+            }
+        }
+    }
+    double Mk[19][19] = {};
+    R rk[19] = {}, pk[19] = {};
+
+    /* MRT in a fixed order: d = f - f^eq; m_k = sum_i M_ki d_i (fused
+     * multiply-adds over the non-zero M_ki in index order, from +0);
+     * n_k = m_k s_k / |M_k|^2; f_i - sum_k M_ki n_k (same order); with
+     * forcing, + sum_k M_ki t_k, t_k = (sum_i M_ki S_i)(1 - s_k / 2) / |M_k|^2.
+     * M is orthogonal, so sum_k M_ki x_k / |M_k|^2 is M^-1 x. */
+    void collide_mrt(R* f, const R* feq, const R* S) const {
+        R d[19], n[19], t[19] = {};
+        for (int i = 0; i < 19; ++i) d[i] = f[i] - feq[i];
+        for (int k = 0; k < 19; ++k) {
+            R m = 0, sm = 0;
+            for (int i = 0; i < 19; ++i)
+                if (Mk[k][i] != 0.0) {
+                    m = fmaR((R)Mk[k][i], d[i], m);
+                    if (force) sm = fmaR((R)Mk[k][i], S[i], sm);
+                }
+            n[k] = m * rk[k];
+            if (force) t[k] = sm * pk[k];
+        }
+        for (int i = 0; i < 19; ++i) {
+            R acc = 0, acc2 = 0;
+            for (int k = 0; k < 19; ++k)
+                if (Mk[k][i] != 0.0) {
+                    acc = fmaR((R)Mk[k][i], n[k], acc);
+                    if (force) acc2 = fmaR((R)Mk[k][i], t[k], acc2);
+                }
+            f[i] = force ? (f[i] - acc) + acc2 : f[i] - acc;
+        }
     }
 
     /* sum_a c_a * v_a over the non-zero components, in axis order:
@@ -240,7 +323,9 @@ struct Ordered {
         R feq[27], Bp[27] = {}, S[27] = {};
         equilibrium(rho, u, feq, Bp);
         if (force) source(u, Bp, S);
-        if (L->p.collision == ORC_SRT) {
+        if (L->p.collision == ORC_MRT) {
+            collide_mrt(f, feq, S);
+        } else if (L->p.collision == ORC_SRT) {
             for (int i = 0; i < vs.q; ++i)
                 f[i] = force ? fmaR(c1, f[i], fmaR(om, feq[i], cSp * S[i]))
                              : fmaR(c1, f[i], om * feq[i]);
@@ -274,6 +359,29 @@ struct Ordered {
         velocity(rho, j, u);
     }
 };
+
+/* inverse of a 19 x 19 matrix by Gauss-Jordan elimination with partial pivoting */
+void invert19(const double (*A)[19], double (*X)[19]) {
+    double a[19][38];
+    for (int r = 0; r < 19; ++r)
+        for (int c = 0; c < 38; ++c) a[r][c] = c < 19 ? A[r][c] : (c - 19 == r ? 1.0 : 0.0);
+    for (int col = 0; col < 19; ++col) {
+        int piv = col;
+        for (int r = col + 1; r < 19; ++r)
+            if (std::fabs(a[r][col]) > std::fabs(a[piv][col])) piv = r;
+        for (int c = 0; c < 38; ++c) std::swap(a[col][c], a[piv][c]);
+        const double d = a[col][col];
+        for (int c = 0; c < 38; ++c) a[col][c] /= d;
+        for (int r = 0; r < 19; ++r)
+            if (r != col) {
+                const double m = a[r][col];
+                if (m != 0.0)
+                    for (int c = 0; c < 38; ++c) a[r][c] -= m * a[col][c];
+            }
+    }
+    for (int r = 0; r < 19; ++r)
+        for (int c = 0; c < 19; ++c) X[r][c] = a[r][19 + c];
+}
 
 /* ------------------------------------------------------------------------ */
 /* Definition in FP64 (DEF64).                                               */
@@ -326,7 +434,27 @@ struct Definition {
             S[i] = vs.w[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
         }
         const double omega = 1.0 / L->p.tau;
-        if (L->p.collision == ORC_SRT) {
+        if (L->p.collision == ORC_MRT) {
+            /* f* = f - M^-1 S_diag M (f - f^eq) + M^-1 (I - S_diag / 2) M S_guo */
+            double M[19][19], Minv[19][19], s[19], m[19], g[19];
+            for (int k = 0; k < 19; ++k)
+                for (int i = 0; i < 19; ++i) M[k][i] = mrt_entry(k, vs.c[i]);
+            invert19(M, Minv);
+            mrt_rates(L->p.tau, s);
+            for (int k = 0; k < 19; ++k) {
+                double neq = 0.0, src = 0.0;
+                for (int i = 0; i < 19; ++i) {
+                    neq += M[k][i] * (f[i] - feq[i]);
+                    src += M[k][i] * S[i];
+                }
+                m[k] = -s[k] * neq + (1.0 - 0.5 * s[k]) * src;
+            }
+            for (int i = 0; i < 19; ++i) {
+                g[i] = f[i];
+                for (int k = 0; k < 19; ++k) g[i] += Minv[i][k] * m[k];
+            }
+            for (int i = 0; i < 19; ++i) f[i] = g[i];
+        } else if (L->p.collision == ORC_SRT) {
             for (int i = 0; i < vs.q; ++i)
                 f[i] = f[i] - omega * (f[i] - feq[i]) + (1.0 - 0.5 * omega) * S[i];
         } else {
@@ -499,7 +627,8 @@ orc_lattice* orc_create(const orc_params* p) {
     if (!p || p->nx < 1 || p->ny < 1 || p->nz < 1) return nullptr;
     if (orc_velset_q(p->velset) == 0) return nullptr;
     if (p->velset == ORC_D2Q9 && p->nz != 1) return nullptr;
-    if (p->collision != ORC_SRT && p->collision != ORC_TRT) return nullptr;
+    if (p->collision != ORC_SRT && p->collision != ORC_TRT && p->collision != ORC_MRT) return nullptr;
+    if (p->collision == ORC_MRT && p->velset != ORC_D3Q19) return nullptr;
     if (!(p->tau > 0.5)) return nullptr;
     if (p->arith == ORC_ARITH_DEF64 && p->storage != ORC_FP64) return nullptr;
     if (p->arith == ORC_ARITH_ORD64 && p->storage != ORC_FP64 && p->storage != ORC_FP32) return nullptr;
@@ -625,3 +754,11 @@ int orc_threads(void) {
 }
 
 }  // extern "C"
+
+void orc_mrt_basis(double* M) {
+    const VelSet vs = make_velset(ORC_D3Q19);
+    for (int k = 0; k < 19; ++k)
+        for (int i = 0; i < 19; ++i) M[k * 19 + i] = mrt_entry(k, vs.c[i]);
+}
+
+void orc_mrt_rates(double tau, double* s) { mrt_rates(tau, s); }

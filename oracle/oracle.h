@@ -43,7 +43,7 @@ enum {
     ORC_P16_0S = 5, ORC_P16_1S = 6, ORC_P16_2C = 7, ORC_P16_0 = 8, ORC_P16_1 = 9
 };
 enum { ORC_D2Q9 = 0, ORC_D3Q19 = 1, ORC_D3Q27 = 2 };
-enum { ORC_SRT = 0, ORC_TRT = 1 };
+enum { ORC_SRT = 0, ORC_TRT = 1, ORC_MRT = 2 };   /* MRT: D3Q19 only */
 enum { ORC_ARITH_DEF64 = 0, ORC_ARITH_ORD32 = 1, ORC_ARITH_ORD64 = 2 };
 
 /* cell flag bits */
@@ -68,7 +68,7 @@ typedef struct {
     int nx, ny, nz;
     int velset;        /* ORC_D2Q9 (nz must be 1; every z component of velocity,
                           force and node velocity is ignored), ORC_D3Q19, ORC_D3Q27 */
-    int collision;     /* ORC_SRT, ORC_TRT */
+    int collision;     /* ORC_SRT, ORC_TRT, ORC_MRT (D3Q19) */
     int arith;         /* ORC_ARITH_* */
     int storage;       /* ORC_FP64 for DEF64; any for ORD32; FP64/FP32 for ORD64 */
     double tau;        /* relaxation time, omega = 1/tau */
@@ -106,6 +106,10 @@ void orc_get_rho_u(const orc_lattice* L, double* rho, double* ux, double* uy, do
 void orc_get_f(const orc_lattice* L, double* f);
 /* FP64 sums over non-solid cells of rho and rho*|u|^2/2 */
 void orc_reduce(const orc_lattice* L, double* mass, double* kinetic_energy);
+/* D3Q19 MRT moment basis (19 x 19, row-major, in the shared direction
+ * order) and the relaxation rate of every moment for relaxation time tau */
+void orc_mrt_basis(double* M);
+void orc_mrt_rates(double tau, double* s);
 /* shifted equilibrium of one cell in the given arithmetic mode (q values) */
 void orc_equilibrium(int velset, int arith, double rho, double ux, double uy, double uz, double* feq);
 int  orc_threads(void);

@@ -345,3 +345,85 @@ def test_shifting_wins_back_sixteen_bit_accuracy():
         err[shifting] = np.linalg.norm(u - uref) / np.linalg.norm(uref)
     assert err[True] < 0.05
     assert err[False] > 5 * err[True]
+
+
+# ---------------------------------------------------------------- MRT (D3Q19)
+def test_mrt_basis_is_the_orthogonal_polynomial_basis():
+    """d'Humieres et al. (2002) D3Q19 moments: rows are the stated velocity
+    polynomials, mutually orthogonal; density and momentum rows are exact."""
+    M = oracle.mrt_basis()
+    c, w = oracle.velset("D3Q19")
+    c2 = (c * c).sum(1)
+    assert np.array_equal(M[0], np.ones(19))
+    assert np.array_equal(M[1], 19 * c2 - 30)
+    assert np.array_equal(M[3], c[:, 0]) and np.array_equal(M[5], c[:, 1]) and np.array_equal(M[7], c[:, 2])
+    assert np.array_equal(M[13], c[:, 0] * c[:, 1])
+    G = M @ M.T
+    assert np.array_equal(G, np.diag(np.diag(G)))
+    # equilibrium energy moment: e_eq = rho (-11 + 19 u.u) for the second-order equilibrium
+    rho, u = 1.03, np.array([0.05, -0.02, 0.03])
+    feq = oracle.equilibrium("D3Q19", "DEF64", rho, u) + w
+    assert abs(M[1] @ feq - rho * (-11 + 19 * u @ u)) < 1e-13
+
+
+def _mrt_lattice(arith, storage, shape, seed, force=(0.0, 0.0, 0.0), tau=0.8):
+    geo = W.random_geometry(shape, seed)
+    o = oracle.Lattice(shape[2], shape[1], shape[0], "D3Q19", "MRT", arith, storage, tau=tau, force=force)
+    o.set_geometry(*geo)
+    o.set_rho_u(*W.random_fields(shape, seed + 1))
+    return o
+
+
+def test_mrt_ordered_modes_track_matrix_definition():
+    """DEF64 applies M^-1 from a general matrix inverse; ORD64/ORD32 use the
+    orthogonal form sum_k M_ki x_k / |M_k|^2 in a fixed order."""
+    shape = (5, 6, 7)
+    out = {}
+    for arith, storage in (("DEF64", "FP64"), ("ORD64", "FP64"), ("ORD32", "FP32")):
+        o = _mrt_lattice(arith, storage, shape, 71, force=(1e-5, -2e-5, 1e-5))
+        o.step(30)
+        out[arith] = o.f()
+    scale = np.abs(out["DEF64"]).max()
+    assert np.abs(out["ORD64"] - out["DEF64"]).max() / scale < 1e-13
+    assert np.abs(out["ORD32"] - out["DEF64"]).max() / scale < 2e-5
+
+
+def test_mrt_conserves_mass_and_momentum():
+    n = 6
+    o = oracle.Lattice(n, n, n, "D3Q19", "MRT", "DEF64", "FP64", tau=0.7)
+    o.set_rho_u(*W.random_fields((n, n, n), 73))
+    r0, ux0, uy0, uz0 = o.rho_u()
+    j0 = [(r0 * u).sum() for u in (ux0, uy0, uz0)]
+    o.step(50)
+    r1, ux1, uy1, uz1 = o.rho_u()
+    assert abs(r1.sum() / r0.sum() - 1) < 1e-13
+    for a, u in zip(j0, (ux1, uy1, uz1)):
+        assert abs((r1 * u).sum() - a) < 1e-12
+
+
+def test_mrt_viscosity_from_taylor_green_decay():
+    """The shear moments relax with omega = 1/tau, so the vortex decays with
+    nu = (tau - 1/2)/3 as with SRT (Sec. 4.2 closed form)."""
+    n, u0, tau, T = 32, 0.01, 0.9, 400
+    o = oracle.Lattice(n, n, 1, "D3Q19", "MRT", "DEF64", "FP64", tau=tau)
+    o.set_rho_u(*W.taylor_green_extruded(n, u0, nz=1))
+    e0 = o.reduce()[1]
+    o.step(T)
+    e1 = o.reduce()[1]
+    nu, k = (tau - 0.5) / 3, 2 * math.pi / n
+    # within the discretisation error at n = 32 (SRT itself: 2e-3)
+    assert abs(np.log(e1 / e0) / (-4 * nu * k * k * T) - 1) < 1e-2
+
+
+def test_mrt_poiseuille_curvature():
+    """Steady plane Poiseuille under MRT: the profile's curvature is -F/nu."""
+    nx, ny, nz, tau, F = 1, 34, 1, 0.8, 1e-6
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "MRT", "DEF64", "FP64", tau=tau, force=(F, 0, 0))
+    o.set_geometry(W.poiseuille_plate(nx, ny, nz))
+    o.set_rho_u()
+    o.step(40000)
+    ux = o.rho_u()[1][0, 1:-1, 0]
+    y = np.arange(1, ny - 1, dtype=float)
+    a = np.polyfit(y, ux, 2)[0]
+    nu = (tau - 0.5) / 3
+    assert abs(2 * a / (-F / nu) - 1) < 1e-6
