@@ -48,8 +48,12 @@ typedef enum {
 
 /* velocity sets (Sec. 2.1; D3Q19 main, D2Q9 and D3Q27 variants) */
 enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1, LBM_D3Q27 = 2 };
-/* collision operators (Sec. 2.1: single- and two-relaxation-time) */
-enum { LBM_SRT = 0, LBM_TRT = 1 };
+/* collision operators: single- and two-relaxation-time (Sec. 2.1), and the
+ * D3Q19 multiple-relaxation-time operator of the Sec. 5 roofline, which the
+ * paper does not define: the orthogonal moment basis and relaxation rates of
+ * d'Humieres et al. (2002), shear and conserved moments relaxed with 1/tau,
+ * the second-order equilibrium and Guo source of the other operators */
+enum { LBM_SRT = 0, LBM_TRT = 1, LBM_MRT = 2 };
 /* storage formats of the populations (Sec. 3, Table 2).  P16_0 / P16_1 are
  * the posit formats of Sec. 3.2 without the 2^7 scaling. */
 enum {
@@ -74,7 +78,8 @@ enum { LBM_STREAM_AB = 0, LBM_STREAM_AA = 1 };
 typedef struct {
     int nx, ny, nz;     /* lattice size; D2Q9 requires nz == 1 */
     int velset;         /* LBM_D2Q9, LBM_D3Q19, LBM_D3Q27 */
-    int collision;      /* LBM_SRT, LBM_TRT */
+    int collision;      /* LBM_SRT, LBM_TRT, LBM_MRT (D3Q19; FP64/FP64, FP32/FP32,
+                           FP32/FP16S and FP32/FP16C; others LBM_ERR_UNSUPPORTED) */
     int storage;        /* LBM_FP64 .. LBM_P16_1 */
     int arith;          /* LBM_ARITH_FP32; LBM_ARITH_FP64 only with FP64/FP32 storage */
     int scheme;         /* LBM_STREAM_AB, LBM_STREAM_AA */

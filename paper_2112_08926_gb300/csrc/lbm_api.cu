@@ -19,7 +19,7 @@ using namespace lbm;
 
 namespace lbm {
 KernelSet& kernel_set(int velset, int collision, int storage, int arith) {
-    static KernelSet table[3][2][10][2];
+    static KernelSet table[3][3][10][2];
     return table[velset][collision][storage][arith];
 }
 }  // namespace lbm
@@ -57,6 +57,19 @@ template <class R> void make_relax(const lbm_params& p, Relax<R>& k) {
     for (int a = 0; a < 3; ++a) k.F[a] = (R)p.force[a];
     k.force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;
     k.sh = p.no_ddf_shifting ? (R)0 : (R)1;
+    if (p.collision == LBM_MRT) {   // D3Q19 rates of d'Humieres et al. (2002); shear and conserved: omega
+        const double om = 1.0 / p.tau;
+        const double s[19] = {om, 1.19, 1.4, om, 1.2, om, 1.2, om, 1.2, om, 1.4, om, 1.4, om, om, om, 1.98, 1.98, 1.98};
+        for (int kk = 0; kk < 19; ++kk) {
+            double norm = 0.0;
+            for (int i = 0; i < 19; ++i) {
+                const double e = (double)mrt_m<D3Q19>(kk, i);
+                norm += e * e;
+            }
+            k.mrt_r[kk] = (R)(s[kk] / norm);
+            k.mrt_p[kk] = (R)((1.0 - 0.5 * s[kk]) / norm);
+        }
+    }
 }
 
 bool want_chunked(const lbm_handle* h);
@@ -150,7 +163,8 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
     if (p.nx < 1 || p.ny < 1 || p.nz < 1) return LBM_ERR_ARG;
     if (p.velset < LBM_D2Q9 || p.velset > LBM_D3Q27) return LBM_ERR_ARG;
     if (p.velset == LBM_D2Q9 && p.nz != 1) return LBM_ERR_ARG;
-    if (p.collision != LBM_SRT && p.collision != LBM_TRT) return LBM_ERR_ARG;
+    if (p.collision != LBM_SRT && p.collision != LBM_TRT && p.collision != LBM_MRT) return LBM_ERR_ARG;
+    if (p.collision == LBM_MRT && p.velset != LBM_D3Q19) return LBM_ERR_UNSUPPORTED;
     if (p.storage < LBM_FP64 || p.storage > LBM_P16_1) return LBM_ERR_ARG;
     if (p.arith != LBM_ARITH_FP32 && p.arith != LBM_ARITH_FP64) return LBM_ERR_ARG;
     if (p.scheme != LBM_STREAM_AB && p.scheme != LBM_STREAM_AA) return LBM_ERR_ARG;

@@ -384,7 +384,38 @@ template <class R> struct Relax {
     R F[3];
     R sh;
     int force;
+    R mrt_r[19], mrt_p[19];   // MRT: s_k / |M_k|^2 and (1 - s_k / 2) / |M_k|^2 (D3Q19)
 };
+
+// D3Q19 multiple-relaxation-time basis (d'Humieres et al. 2002): moment k of
+// direction i as a velocity polynomial -- rho, e, epsilon, j_x, q_x, j_y,
+// q_y, j_z, q_z, 3 p_xx, 3 pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x, m_y,
+// m_z.  Every entry is an integer.
+template <class V>
+__host__ __device__ constexpr int mrt_m(int k, int i) {
+    const int x = V::c(i, 0), y = V::c(i, 1), z = V::c(i, 2), c2 = x * x + y * y + z * z;
+    switch (k) {
+    case 0: return 1;
+    case 1: return 19 * c2 - 30;
+    case 2: return (21 * c2 * c2 - 53 * c2 + 24) / 2;
+    case 3: return x;
+    case 4: return (5 * c2 - 9) * x;
+    case 5: return y;
+    case 6: return (5 * c2 - 9) * y;
+    case 7: return z;
+    case 8: return (5 * c2 - 9) * z;
+    case 9: return 3 * x * x - c2;
+    case 10: return (3 * c2 - 5) * (3 * x * x - c2);
+    case 11: return y * y - z * z;
+    case 12: return (3 * c2 - 5) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return x * (y * y - z * z);
+    case 17: return y * (z * z - x * x);
+    default: return z * (x * x - y * y);
+    }
+}
 
 // sum over axes of c_ia * v_a in axis order: the first non-zero term is +-v_a,
 // each later one is added or subtracted (no multiplications)
@@ -516,7 +547,37 @@ __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
     R feq[V::Q], Bp[V::Q], S[V::Q];
     equilibrium<V, R, SL>(rho, u, feq, Bp, k.sh);
     if (k.force) guo_source<V, R, SL>(k, u, Bp, S);
-    if constexpr (COLL == 0) {   // SRT: fma(1 - omega, f, omega f^eq)
+    if constexpr (COLL == 2) {   // MRT (D3Q19): f - M^-1 S M (f - f^eq) [+ M^-1 (I - S/2) M S_guo]
+        static_assert(V::Q == 19, "MRT is defined for D3Q19");
+        // fixed order: sums over the non-zero M_ki in index order from +0
+        R d[19], n[19], t[19];
+        static_for<0, 19>([&](auto I) { d[I.value] = f[I.value] - feq[I.value]; });
+        static_for<0, 19>([&](auto K) {
+            constexpr int kk = K.value;
+            R m = R(0), sm = R(0);
+            static_for<0, 19>([&](auto I) {
+                constexpr int e = mrt_m<V>(kk, I.value);
+                if constexpr (e != 0) {
+                    m = fmaR(R(e), d[I.value], m);
+                    if (k.force) sm = fmaR(R(e), S[I.value], sm);
+                }
+            });
+            n[kk] = m * k.mrt_r[kk];
+            t[kk] = k.force ? sm * k.mrt_p[kk] : R(0);
+        });
+        static_for<0, 19>([&](auto I) {
+            constexpr int i = I.value;
+            R acc = R(0), acc2 = R(0);
+            static_for<0, 19>([&](auto K) {
+                constexpr int e = mrt_m<V>(K.value, i);
+                if constexpr (e != 0) {
+                    acc = fmaR(R(e), n[K.value], acc);
+                    if (k.force) acc2 = fmaR(R(e), t[K.value], acc2);
+                }
+            });
+            f[i] = k.force ? (f[i] - acc) + acc2 : f[i] - acc;
+        });
+    } else if constexpr (COLL == 0) {   // SRT: fma(1 - omega, f, omega f^eq)
         if (k.force) {
             static_for<0, V::Q>([&](auto I) {
                 constexpr int i = I.value;

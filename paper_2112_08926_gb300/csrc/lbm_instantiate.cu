@@ -116,7 +116,9 @@ void fill() {
     // the chunked layout and the paired kernels: 16-bit storage, FP32
     // arithmetic; D3Q27 keeps the generic kernels (27 code pairs per lane do
     // not fit the register budget of the paired kernels)
-    if constexpr (LBM_ARITH == 0 && FMT >= 2 && !std::is_same<V, D3Q27>::value) {
+    // MRT keeps the generic kernels too (its 19 x 19 transforms per cell pair
+    // would double the build for a kernel the operator cannot keep fed)
+    if constexpr (LBM_ARITH == 0 && FMT >= 2 && COLL < 2 && !std::is_same<V, D3Q27>::value) {
         s.probe[LAYOUT_AB_CHUNKED] = launch_probe<V, LAYOUT_AB_CHUNKED>;
         s.probe[LAYOUT_AA_SWAPPED_CHUNKED] = launch_probe<V, LAYOUT_AA_SWAPPED_CHUNKED>;
         s.probe[LAYOUT_AA_NATURAL_CHUNKED] = launch_probe<V, LAYOUT_AA_NATURAL_CHUNKED>;
@@ -129,7 +131,7 @@ void fill() {
             s.list_chunked[PH.value] = launch_list<V, COLL, PH.value, uint32_t, true>;
         });
     }
-    if constexpr (LBM_ARITH == 0 && FMT != 0 && std::is_same<V, D3Q19>::value) {
+    if constexpr (LBM_ARITH == 0 && FMT != 0 && COLL < 2 && std::is_same<V, D3Q19>::value) {
         s.staged[0] = launch_staged<V, COLL, 128>;
         s.staged[1] = launch_staged<V, COLL, 256>;
         s.staged[2] = launch_staged<V, COLL, 512>;
@@ -143,7 +145,14 @@ void fill() {
 struct Registrar {
     Registrar() {
         if constexpr (LBM_VELSET == 0) { fill<D2Q9, 0>(); fill<D2Q9, 1>(); }
-        if constexpr (LBM_VELSET == 1) { fill<D3Q19, 0>(); fill<D3Q19, 1>(); }
+        if constexpr (LBM_VELSET == 1) {
+            fill<D3Q19, 0>();
+            fill<D3Q19, 1>();
+            // MRT for the storage formats of the paper's roofline comparison:
+            // FP64 (FP64 arithmetic), FP32, FP16S and FP16C
+            if constexpr ((FMT == 0 && LBM_ARITH == 1) || (LBM_ARITH == 0 && (FMT == 1 || FMT == 3 || FMT == 4)))
+                fill<D3Q19, 2>();
+        }
         if constexpr (LBM_VELSET == 2) { fill<D3Q27, 0>(); fill<D3Q27, 1>(); }
     }
 };

@@ -38,7 +38,7 @@ struct KernelSet {
     bool present = false;
 };
 
-// velset 0..2, collision 0..1, storage 0..9, arith 0 (FP32) / 1 (FP64)
+// velset 0..2, collision 0..2 (MRT: D3Q19), storage 0..9, arith 0 (FP32) / 1 (FP64)
 KernelSet& kernel_set(int velset, int collision, int storage, int arith);
 
 }  // namespace lbm

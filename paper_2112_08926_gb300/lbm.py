@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(HERE, "_build", "liblbm.so")
 LBM_OK, LBM_ERR_ARG, LBM_ERR_OOM, LBM_ERR_CUDA, LBM_ERR_UNSUPPORTED = 0, 1, 2, 3, 4
 LBM_ERR_DIVERGED, LBM_ERR_TIMEOUT, LBM_ERR_STATE = 5, 6, 7
 VELSETS = {"D2Q9": 0, "D3Q19": 1, "D3Q27": 2}
-COLLISIONS = {"SRT": 0, "TRT": 1}
+COLLISIONS = {"SRT": 0, "TRT": 1, "MRT": 2}
 STORAGES = {"FP64": 0, "FP32": 1, "FP16": 2, "FP16S": 3, "FP16C": 4,
             "P16_0S": 5, "P16_1S": 6, "P16_2C": 7, "P16_0": 8, "P16_1": 9}
 ARITHS = {"FP32": 0, "FP64": 1}

@@ -464,3 +464,60 @@ def test_ensemble_autotune_picks_scheme_bitwise():
     for ga, gb in zip(a, b):
         assert np.array_equal(ga.f(), gb.f())
     e.close()
+
+
+# ---------------------------------------------------------------- MRT (D3Q19)
+@pytest.mark.parametrize("storage", ["FP32", "FP16S", "FP16C"])
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+@pytest.mark.parametrize("shape", [(7, 19, 37), (3, 7, 128)])
+def test_mrt_fp32_arithmetic_bitwise(storage, scheme, shape):
+    """D3Q19 MRT (moment basis and rates of d'Humieres et al. 2002) in the
+    fixed transform order: bit for bit the ordered FP32 oracle, with
+    boundaries and forcing."""
+    nz, ny, nx = shape
+    extra = {"outflow": 0.0, "freeslip_frac": 0.0} if scheme == "AA" else {}
+    geo = W.random_geometry(shape, 81, **extra)
+    fields = W.random_fields(shape, 82)
+    force = (1e-5, -2e-5, 3e-5)
+    steps = 21 if scheme == "AA" else 20
+    g = P().Lattice(nx, ny, nz, "D3Q19", "MRT", storage, "FP32", scheme, tau=0.66, force=force)
+    g.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    g.step(steps)
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "MRT", "ORD32", storage, tau=0.66, force=force)
+    o.set_geometry(*geo)
+    o.set_rho_u(*fields)
+    o.step(steps)
+    assert np.array_equal(g.f(), o.f())
+    g.close()
+
+
+def test_mrt_fp64_tier():
+    shape = (7, 19, 37)
+    nz, ny, nx = shape
+    geo = W.random_geometry(shape, 83)
+    fields = W.random_fields(shape, 84)
+    force = (1e-5, -2e-5, 3e-5)
+    g = P().Lattice(nx, ny, nz, "D3Q19", "MRT", "FP64", "FP64", "AB", tau=0.7, force=force)
+    g.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    g.step(20)
+    gf = g.f()
+    g.close()
+    for arith, check in (("DEF64", "l2"), ("ORD64", "bitwise")):
+        o = oracle.Lattice(nx, ny, nz, "D3Q19", "MRT", arith, "FP64", tau=0.7, force=force)
+        o.set_geometry(*geo)
+        o.set_rho_u(*fields)
+        o.step(20)
+        of = o.f()
+        if check == "l2":
+            assert np.linalg.norm(gf - of) / np.linalg.norm(of) < 1e-12
+        else:
+            assert np.array_equal(gf, of)
+
+
+def test_mrt_unsupported_combinations():
+    for vs, storage, arith, nz in (("D2Q9", "FP32", "FP32", 1), ("D3Q19", "P16_1S", "FP32", 4)):
+        with pytest.raises(P().LBMError) as e:
+            P().Lattice(8, 4, nz, vs, "MRT", storage, arith, "AB")
+        assert e.value.status == 4
