@@ -312,6 +312,29 @@ def karman(P, torch, steps=50000, t0=20000, every=20, tiers=(("FP64", "FP64"), (
     return out
 
 
+def collision_sweep(P, torch, steps, n=256):
+    """SRT, TRT and MRT on the periodic Taylor-Green workload for the tiers of
+    the paper's roofline comparison (Sec. 5: three collision operators per
+    number format): MLUPs/s and the HBM fraction of each."""
+    import workloads as W
+    peak, _ = peaks()
+    fields = W.taylor_green_extruded(n, 0.05)
+    rows = []
+    for arith, storage in (("FP64", "FP64"), ("FP32", "FP32"), ("FP32", "FP16S"), ("FP32", "FP16C")):
+        for coll in ("SRT", "TRT", "MRT"):
+            g = P.Lattice(n, n, n, "D3Q19", coll, storage, arith, "AB", tau=0.53)
+            g.set_rho_u(*fields)
+            g.step(5)
+            st = max(10, steps // (8 if arith == "FP64" else 1))
+            dt = time_steps(torch, g, st)
+            b = 2 * 19 * pop_bytes(storage)
+            rows.append({"tier": f"{arith}/{storage}", "collision": coll, "variant": g.variant(),
+                         "mlups": n ** 3 * st / dt / 1e6, "frac_hbm": b * n ** 3 * st / dt / 1e9 / peak})
+            g.close()
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return rows
+
+
 def bench_reference(args, rank, world):
     if rank != 0:
         return
@@ -356,6 +379,8 @@ def main():
     ap.add_argument("--cavity-sweep", action="store_true",
                     help="only the D3Q19 TRT lid-driven cavity size sweep (one JSON line)")
     ap.add_argument("--cavity-sizes", default="", help="comma-separated subset of the sweep's edge lengths")
+    ap.add_argument("--collisions", action="store_true",
+                    help="only SRT / TRT / MRT per number format on the Taylor-Green workload")
     ap.add_argument("--karman", action="store_true",
                     help="only the Karman vortex street accuracy run (Strouhal number, L2 vs FP64)")
     args = ap.parse_args()
@@ -375,6 +400,11 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2112_08926_gb300 as P
+
+    if args.collisions:
+        if rank == 0:
+            print(json.dumps({"collisions": collision_sweep(P, torch, args.steps)}), flush=True)
+        return
 
     if args.karman:
         if rank == 0:
