@@ -335,6 +335,31 @@ def collision_sweep(P, torch, steps, n=256):
     return rows
 
 
+def velset_sweep(P, torch, steps):
+    """D2Q9, D3Q19 and D3Q27 SRT on the periodic Taylor-Green workload (the
+    velocity sets of the paper's roofline, Sec. 5), 16.8 M cells each
+    (4096^2 for D2Q9, 256^3 otherwise): MLUPs/s and the HBM fraction for
+    FP32, FP16S and FP16C storage with FP32 arithmetic."""
+    import workloads as W
+    peak, _ = peaks()
+    rows = []
+    for vs, q, (nx, ny, nz) in (("D2Q9", 9, (4096, 4096, 1)), ("D3Q19", 19, (256, 256, 256)),
+                                ("D3Q27", 27, (256, 256, 256))):
+        fields = W.taylor_green_extruded(nx, 0.05, nz=nz, ny=ny)
+        for storage in ("FP32", "FP16S", "FP16C"):
+            g = P.Lattice(nx, ny, nz, vs, "SRT", storage, "FP32", "AB", tau=0.53)
+            g.set_rho_u(*fields)
+            g.step(5)
+            dt = time_steps(torch, g, steps)
+            cells, b = nx * ny * nz, 2 * q * pop_bytes(storage)
+            rows.append({"velset": vs, "storage": storage, "variant": g.variant(), "cells": cells,
+                         "mlups": cells * steps / dt / 1e6, "bytes_per_cell": b,
+                         "frac_hbm": b * cells * steps / dt / 1e9 / peak})
+            g.close()
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    return rows
+
+
 def bench_reference(args, rank, world):
     if rank != 0:
         return
@@ -381,6 +406,8 @@ def main():
     ap.add_argument("--cavity-sizes", default="", help="comma-separated subset of the sweep's edge lengths")
     ap.add_argument("--collisions", action="store_true",
                     help="only SRT / TRT / MRT per number format on the Taylor-Green workload")
+    ap.add_argument("--velsets", action="store_true",
+                    help="D2Q9 / D3Q19 / D3Q27 throughput per storage format instead of the default run")
     ap.add_argument("--karman", action="store_true",
                     help="only the Karman vortex street accuracy run (Strouhal number, L2 vs FP64)")
     args = ap.parse_args()
@@ -404,6 +431,11 @@ def main():
     if args.collisions:
         if rank == 0:
             print(json.dumps({"collisions": collision_sweep(P, torch, args.steps)}), flush=True)
+        return
+
+    if args.velsets:
+        if rank == 0:
+            print(json.dumps({"velsets": velset_sweep(P, torch, args.steps)}), flush=True)
         return
 
     if args.karman:

@@ -252,20 +252,29 @@ extern "C" lbm_status lbm_set_block(lbm_handle* h, int bx, int by) {
 namespace {
 
 // Lists the non-solid cells whose flag byte is not 0 (after the internal
-// neighbour bits are set).  count[0] must start at 0; with out == NULL only
-// counts.  One atomic per warp; a warp's cells keep their order.
-__global__ void k_list_special(const uint8_t* __restrict__ flags, size_t N, uint32_t* count, uint32_t* out) {
+// neighbour bits are set), in two parts: the cells with a rule beyond plain
+// bounce-back (out, counted in count[0]) and the plain bounce-back cells,
+// byte F_NEAR_SOLID alone (out_bb, count[1]).  The counters must start at 0;
+// with null outputs the kernel only counts.  One atomic per warp and part; a
+// warp's cells keep their order.
+__global__ void k_list_special(const uint8_t* __restrict__ flags, size_t N, uint32_t* count, uint32_t* out,
+                               uint32_t* out_bb) {
     const int lane = threadIdx.x & 31;
+    const uint32_t below = (1u << lane) - 1u;
     for (size_t base = ((size_t)blockIdx.x * blockDim.x + threadIdx.x) & ~(size_t)31; base < N;
          base += (size_t)gridDim.x * blockDim.x) {
         const size_t n = base + lane;
         const uint32_t fl = n < N ? flags[n] : 0u;
-        const bool sp = fl != 0u && !(fl & F_WALL);
-        const uint32_t mask = __ballot_sync(0xffffffffu, sp);
-        uint32_t at = 0;
-        if (lane == 0 && mask) at = atomicAdd(count, (uint32_t)__popc(mask));
+        const bool bb = fl == F_NEAR_SOLID;
+        const bool sp = fl != 0u && !(fl & F_WALL) && !bb;
+        const uint32_t m_sp = __ballot_sync(0xffffffffu, sp), m_bb = __ballot_sync(0xffffffffu, bb);
+        uint32_t at = 0, at_bb = 0;
+        if (lane == 0 && m_sp) at = atomicAdd(count, (uint32_t)__popc(m_sp));
+        if (lane == 0 && m_bb) at_bb = atomicAdd(count + 1, (uint32_t)__popc(m_bb));
         at = __shfl_sync(0xffffffffu, at, 0);
-        if (sp && out) out[at + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)n;
+        at_bb = __shfl_sync(0xffffffffu, at_bb, 0);
+        if (sp && out) out[at + __popc(m_sp & below)] = (uint32_t)n;
+        if (bb && out_bb) out_bb[at_bb + __popc(m_bb & below)] = (uint32_t)n;
     }
 }
 
@@ -295,7 +304,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         h->has_open_boundaries = false;
         h->release((void*&)h->special, (size_t)h->special_cap * sizeof(uint32_t));
         h->special_cap = 0;
-        h->n_special = 0;
+        h->n_special = h->n_complex = 0;
         h->release((void*&)h->flags, N);
         h->release((void*&)h->node_u, 3 * N * sizeof(float));
         h->release((void*&)h->node_rho, N * sizeof(float));
@@ -367,28 +376,31 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         else k_mark_neighbours<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
         if (h->cuda(cudaGetLastError(), "mark kernel")) return LBM_ERR_CUDA;
     }
-    {   // list of the non-plain cells (two passes: count, then fill)
+    {   // list of the non-plain cells (two passes: count, then fill): the
+        // cells with other rules first, then the plain bounce-back cells
         h->release((void*&)h->special, (size_t)h->special_cap * sizeof(uint32_t));
         h->special_cap = 0;
-        h->n_special = 0;
+        h->n_special = h->n_complex = 0;
         uint32_t* cnt = reinterpret_cast<uint32_t*>(h->partial);   // scratch word pair
         const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
-        if (h->cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), h->stream), "memset")) return LBM_ERR_CUDA;
-        k_list_special<<<grid, 256, 0, h->stream>>>(h->flags, N, cnt, nullptr);
+        if (h->cuda(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), h->stream), "memset")) return LBM_ERR_CUDA;
+        k_list_special<<<grid, 256, 0, h->stream>>>(h->flags, N, cnt, nullptr, nullptr);
         if (h->cuda(cudaGetLastError(), "list kernel")) return LBM_ERR_CUDA;
-        uint32_t count = 0;
-        if (h->cuda(cudaMemcpyAsync(&count, cnt, sizeof count, cudaMemcpyDeviceToHost, h->stream), "download") ||
+        uint32_t count[2] = {0, 0};
+        if (h->cuda(cudaMemcpyAsync(count, cnt, sizeof count, cudaMemcpyDeviceToHost, h->stream), "download") ||
             h->cuda(cudaStreamSynchronize(h->stream), "sync"))
             return LBM_ERR_CUDA;
-        if (count > 0) {
-            h->special = (uint32_t*)h->alloc((size_t)count * sizeof(uint32_t));
+        const uint32_t total = count[0] + count[1];
+        if (total > 0) {
+            h->special = (uint32_t*)h->alloc((size_t)total * sizeof(uint32_t));
             if (!h->special) return h->fail(LBM_ERR_OOM, "cell list");
-            h->special_cap = count;
-            if (h->cuda(cudaMemsetAsync(cnt, 0, sizeof(uint32_t), h->stream), "memset")) return LBM_ERR_CUDA;
-            k_list_special<<<grid, 256, 0, h->stream>>>(h->flags, N, cnt, h->special);
+            h->special_cap = total;
+            if (h->cuda(cudaMemsetAsync(cnt, 0, 2 * sizeof(uint32_t), h->stream), "memset")) return LBM_ERR_CUDA;
+            k_list_special<<<grid, 256, 0, h->stream>>>(h->flags, N, cnt, h->special, h->special + count[0]);
             if (h->cuda(cudaGetLastError(), "list kernel")) return LBM_ERR_CUDA;
         }
-        h->n_special = count;
+        h->n_special = total;
+        h->n_complex = count[0];
     }
     lbm_status st2 = ensure_layout(h);
     if (st2 != LBM_OK) return st2;
@@ -627,7 +639,7 @@ lbm_status ensure_layout(lbm_handle* h) {
 
 template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, cudaStream_t s) {
     const int scheme = h->scheme_now();
-    const StepArgs<R> a = h->args(k, h->aa() ? 0 : h->cur);
+    StepArgs<R> a = h->args(k, h->aa() ? 0 : h->cur);
     const int variant = variant_in_use(h);
     lbm_status st;
     if (h->chunked) {
@@ -635,13 +647,19 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
         L.block = dim3(32, 8, 1);
         L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
         L.stream = s;
+        // prefetch one plane beyond the planes the resident blocks (3 per SM) cover
+        const long per_plane = (long)L.grid.x * L.grid.y, resident = 3L * h->num_sms;
+        a.pf = (int)std::min<long>(8, (resident + per_plane - 1) / per_plane + 1);
         st = h->cuda(h->ks->pair_chunked[scheme][h->flags ? 1 : 0](&a, L), "chunked step kernel");
-        if (st == LBM_OK && h->flags && h->n_special > 0) {   // the non-plain cells
+        // the non-plain cells; the paired kernel updates the plain bounce-back
+        // cells itself except in the odd A-A half
+        const uint32_t nl = scheme == lbm::SCHEME_AA_PP ? h->n_special : h->n_complex;
+        if (st == LBM_OK && h->flags && nl > 0) {
             Launch B;
             B.block = dim3(256);
-            B.grid = dim3((h->n_special + 255) / 256);
+            B.grid = dim3((nl + 255) / 256);
             B.stream = s;
-            st = h->cuda(h->ks->list_chunked[scheme](&a, h->special, h->n_special, B), "list kernel");
+            st = h->cuda(h->ks->list_chunked[scheme](&a, h->special, nl, B), "list kernel");
         }
     } else if (variant == LBM_VARIANT_PAIRED) {
         Launch L;
@@ -658,12 +676,14 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
     } else {
         st = h->cuda(h->ks->step[scheme][h->flags ? 1 : 0][h->idx32() ? 1 : 0](&a, h->step_launch(s)),
                      "step kernel");
-        if (st == LBM_OK && h->flags && h->n_special > 0) {   // the non-plain cells
+        // the non-plain cells except the plain bounce-back ones, which the
+        // step kernel updates itself
+        if (st == LBM_OK && h->flags && h->n_complex > 0) {
             Launch L;
             L.block = dim3(256);
-            L.grid = dim3((h->n_special + 255) / 256);
+            L.grid = dim3((h->n_complex + 255) / 256);
             L.stream = s;
-            st = h->cuda(h->ks->list[scheme][h->idx32() ? 1 : 0](&a, h->special, h->n_special, L), "list kernel");
+            st = h->cuda(h->ks->list[scheme][h->idx32() ? 1 : 0](&a, h->special, h->n_complex, L), "list kernel");
         }
     }
     if (st != LBM_OK) return st;

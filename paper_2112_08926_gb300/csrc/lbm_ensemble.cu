@@ -83,6 +83,8 @@ std::vector<EnsMember<R>> make_table(lbm_ensemble* e, std::vector<uint32_t>& til
         EnsMember<R>& M = tab[k];
         M.args[0] = h->args(rk, e->aa ? 0 : h->cur);
         M.args[1] = h->args(rk, e->aa ? 0 : 1 - h->cur);
+        // L2 prefetch distance in tiles: the tiles that fit on the GPU at once
+        M.args[0].pf = M.args[1].pf = h->num_sms * (2048 / e->tile);
         M.ncells = (uint32_t)h->N;
         M.tile0 = total;
         M.by_plane = make_div((uint32_t)h->plane());
@@ -120,20 +122,20 @@ lbm_status upload_table(lbm_ensemble* e) {
     if (e->cuda(cudaMemcpyAsync(e->tile_member, tiles.data(), tiles.size() * sizeof(uint32_t),
                                 cudaMemcpyHostToDevice, e->stream), "table upload"))
         return LBM_ERR_CUDA;
-    if (!e->list) {   // the members' lists of non-plain cells, concatenated
+    if (!e->list) {   // the members' non-plain cells beyond plain bounce-back (the step kernel updates those), concatenated
         size_t total = 0;
-        for (lbm_handle* h : e->m) total += h->n_special;
+        for (lbm_handle* h : e->m) total += h->n_complex;
         if (total > 0xFFFFFFFFull) return LBM_ERR_UNSUPPORTED;
         if (total > 0) {
             if (e->cuda(cudaMalloc((void**)&e->list, total * sizeof(uint64_t)), "list alloc")) return LBM_ERR_OOM;
             size_t at = 0;
             for (size_t k = 0; k < e->m.size(); ++k) {
                 const lbm_handle* h = e->m[k];
-                if (!h->n_special) continue;
-                k_tag_cells<<<(unsigned)std::min<size_t>((h->n_special + 255) / 256, 1024), 256, 0, e->stream>>>(
-                    h->special, h->n_special, (uint32_t)k, e->list + at);
+                if (!h->n_complex) continue;
+                k_tag_cells<<<(unsigned)std::min<size_t>((h->n_complex + 255) / 256, 1024), 256, 0, e->stream>>>(
+                    h->special, h->n_complex, (uint32_t)k, e->list + at);
                 if (e->cuda(cudaGetLastError(), "list kernel")) return LBM_ERR_CUDA;
-                at += h->n_special;
+                at += h->n_complex;
             }
         }
         e->n_list = (uint32_t)total;

@@ -31,6 +31,7 @@ struct lbm_handle {
     size_t scratch_doubles = 0;
     uint32_t* special = nullptr;   // cells that are not plain fluid (flagged lattices)
     uint32_t n_special = 0, special_cap = 0;
+    uint32_t n_complex = 0;   // leading part of `special`: cells with rules beyond plain bounce-back
     bool has_open_boundaries = false;   // OUTFLOW or FREESLIP cells (A-B only)
     double* partial = nullptr;
     int64_t t = 0;

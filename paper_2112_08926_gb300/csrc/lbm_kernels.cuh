@@ -42,8 +42,11 @@ enum { PROBE_FIELDS = 0, PROBE_F = 1, PROBE_REDUCE = 2 };
 
 // internal flag bits of non-solid cells, set by the library after upload:
 // a neighbour is solid (or the cell is an outflow cell), a neighbour is a
-// moving wall
+// free-slip wall, a neighbour is a moving wall.  A cell whose byte is
+// F_NEAR_SOLID alone needs plain bounce-back only (no moving, free-slip,
+// equilibrium or outflow rule): the fast kernels update it themselves.
 constexpr uint32_t F_NEAR_SOLID = 0x20u;
+constexpr uint32_t F_NEAR_FREESLIP = 0x40u;
 constexpr uint32_t F_NEAR_MOVING = 0x80u;
 
 template <class R> struct StepArgs {
@@ -55,6 +58,7 @@ template <class R> struct StepArgs {
     int nx, ny, nz;
     uint32_t N;
     Relax<R> k;
+    int pf;                   // L2 prefetch distance: z-planes (chunked kernels), tiles (ensemble); 0: none
 };
 
 struct Nbr {
@@ -100,6 +104,14 @@ template <class V, int I, class R, int SL>
 __device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t m) {
     const R uw[3] = {(R)node_u[m], (R)node_u[N + m], (R)node_u[2 * N + m]};
     return R(6.0 * V::w(I) * Pow2<SL>::up) * csum<V, I, R>(uw);
+}
+
+// Bit i set: the upstream cell x - c_i of the cell at `nb` is solid.
+template <class V>
+__device__ __forceinline__ uint32_t solid_upstream(const uint8_t* __restrict__ flags, const Nbr& nb) {
+    uint32_t m = 0;
+    static_for<1, V::Q>([&](auto I) { m |= ((uint32_t)flags[nb.up<V, I.value>()] & F_WALL) << I.value; });
+    return m;
 }
 
 // Streamed populations of a cell next to solid cells (or an outflow cell),
@@ -214,7 +226,22 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
     R f[V::Q];
     uint32_t walls = 0;   // directions with a solid upstream (= downstream of the opposite) cell
     if constexpr (SPEC) gather<V, FMT, R, false, LAYOUT, IX>(a, src, x, y, z, n, 0u, f);
-    if (PLAIN_ONLY && fl != 0u) return;
+    if (PLAIN_ONLY && fl != 0u) {
+        // plain bounce-back cells stay: a direction whose upstream cell is
+        // solid takes the cell's own opposite population instead, as in
+        // gather_boundary (the even A-A half reads own slots only and has
+        // nothing to replace); every other non-plain cell is listed
+        if (fl != F_NEAR_SOLID) return;
+        if constexpr (PH != LAYOUT_AA_NATURAL) {
+            const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
+            walls = solid_upstream<V>(a.flags, nb);
+            static_for<1, V::Q>([&](auto I) {
+                constexpr int i = I.value;
+                constexpr int bslot = PH == LAYOUT_AA_SWAPPED ? i : opposite(i);
+                if ((walls >> i) & 1u) f[i] = S::template load_g<R>(elem_ptr<IX, CH, V>(src, bslot, a.N, n), 0u);
+            });
+        }
+    }
     if (FLAGS && (fl & F_WALL)) return;
     if (FLAGS && (fl & F_EQ)) {
         const R u[3] = {(R)a.node_u[n], (R)a.node_u[(size_t)a.N + n], (R)a.node_u[2 * (size_t)a.N + n]};
@@ -234,7 +261,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
         });
     } else {
         const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
-        if (FLAGS && (fl & F_NEAR_SOLID)) {
+        if ((FLAGS || PLAIN_ONLY) && (fl & F_NEAR_SOLID)) {
             static_for<0, V::Q>([&](auto I) {
                 constexpr int i = I.value;
                 const uint32_t d = nb.down<V, i>();
@@ -519,9 +546,10 @@ template <> struct PairCodec<3> : PairCodecHalf<3> {};
 //     store (every location is written by the warp whose cell read it).
 //   PHASE LAYOUT_AA_NATURAL (even A-A half): read own slot i, write own slot
 //     opposite(i); no shifts.
-// PLAIN (flagged lattice): only cells whose flag byte is 0 are written; a
-// pair with one such cell is written as a single 16-bit code; the other
-// cells belong to the list kernel.
+// PLAIN (flagged lattice): only cells whose flag byte is 0 are written, and
+// in the A-B and even A-A halves the plain bounce-back cells (byte
+// F_NEAR_SOLID); a pair with one such cell is written as a single 16-bit
+// code; the other cells belong to the list kernel.
 template <class V, int COLL, int FMT, int PHASE, bool PLAIN>
 __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<float> a) {
     using PC = PairCodec<FMT>;
@@ -542,11 +570,35 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
     const uint16_t* src = (const uint16_t*)a.src;
     uint16_t* dst = (uint16_t*)a.dst;
     const uint32_t own_chunk = (ry[1] + rz[1]) * XT + X;   // < 2^25: N < 2^31 cells
-    uint32_t pl = 3u;   // bit 0: cell 2l is plain, bit 1: cell 2l + 1
+    // Blocks start in launch order (x, then y, then z), so the warp at the
+    // same chunk and row pf planes further runs about one wave later: this
+    // warp sends its q lines (and, flagged, its flag line) into L2 ahead of
+    // it.  Nothing waits on these prefetches, so they keep HBM busy beyond
+    // the loads the registers of the resident warps can hold; the bytes read
+    // from HBM stay the same.  Only the formats with hardware conversion are
+    // bound by HBM; the others are bound by instruction issue and skip it.
+    if constexpr (FMT == 2 || FMT == 3) {
+        const int zf = z + a.pf;
+        if (a.pf > 0 && zf < a.nz) {
+            const uint32_t fut = (ry[1] + (uint32_t)zf * ny) * XT + X;
+            if (lane < V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)fut * CHE + lane * CHUNK));
+            else if (PLAIN && lane == V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.flags + (size_t)fut * CHUNK));
+        }
+    }
+    uint32_t pl = 3u;   // bit 0: cell 2l is updated here, bit 1: cell 2l + 1
+    uint32_t bb = 0u;   // the same bits for plain bounce-back cells (A-B)
     if constexpr (PLAIN) {
         const uint32_t fl2 = reinterpret_cast<const uint16_t*>(a.flags)[own_chunk * (CHUNK / 2) + lane];
-        pl = ((fl2 & 0xFFu) == 0u ? 1u : 0u) | ((fl2 >> 8) == 0u ? 2u : 0u);
-        if (!__any_sync(0xffffffffu, pl != 0u)) return;   // nothing plain in this chunk
+        const uint32_t f0 = fl2 & 0xFFu, f1 = fl2 >> 8;
+        pl = (f0 == 0u ? 1u : 0u) | (f1 == 0u ? 2u : 0u);
+        // plain bounce-back cells: A-B replaces their wall directions below;
+        // the even A-A half treats them as plain; the odd half leaves them
+        // to the list kernel (their pushes into solid cells turn back)
+        if constexpr (PHASE != LAYOUT_AA_SWAPPED) {
+            bb = (f0 == F_NEAR_SOLID ? 1u : 0u) | (f1 == F_NEAR_SOLID ? 2u : 0u);
+            pl |= bb;
+        }
+        if (!__any_sync(0xffffffffu, pl != 0u)) return;   // nothing to update in this chunk
     }
     uint32_t g[V::Q];   // lo half: cell 2*lane, hi half: cell 2*lane + 1 (of this chunk)
     if constexpr (PHASE == LAYOUT_AA_NATURAL) {
@@ -581,6 +633,26 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
                 }
             });
         });
+    }
+    if constexpr (PLAIN && PHASE == LAYOUT_AB) {
+        // plain bounce-back: a direction whose upstream cell is solid takes
+        // the code of the cell's own opposite population, from its own row
+        if (__any_sync(0xffffffffu, bb != 0u)) {
+            const uint16_t* own = src + (size_t)own_chunk * CHE + 2 * lane;
+#pragma unroll 1
+            for (int h = 0; h < 2; ++h) {
+                if (!((bb >> h) & 1u)) continue;
+                const Nbr nb((int)(X * CHUNK) + 2 * lane + h, y, z, a.nx, a.ny, a.nz);
+                const uint32_t walls = solid_upstream<V>(a.flags, nb);
+                static_for<1, V::Q>([&](auto I) {
+                    constexpr int i = I.value;
+                    if ((walls >> i) & 1u) {
+                        const uint32_t c = own[opposite(i) * CHUNK + h];
+                        g[i] = h ? ((g[i] & 0xFFFFu) | (c << 16)) : ((g[i] & 0xFFFF0000u) | c);
+                    }
+                });
+            }
+        }
     }
     float fa[V::Q], fb[V::Q];
     static_for<0, V::Q>([&](auto I) { fa[I.value] = PC::dec(g[I.value]).x; });
@@ -647,12 +719,43 @@ template <class R> struct EnsMember {
     FastDiv by_plane, by_nx;
 };
 
+// L2 prefetch for the tile a.pf tiles further in launch order (about one
+// wave later, since blocks start in launch order): its q population ranges
+// and its flag bytes, one 128-byte line per thread; the bytes read from HBM
+// stay the same.  16-bit formats with hardware conversion only (HBM-bound).
+template <class V, int FMT, class R>
+__device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restrict__ members,
+                                                    const uint32_t* __restrict__ tile_member, int parity, int pf) {
+    if constexpr (FMT == 2 || FMT == 3) {
+        using T = typename Storage<FMT>::T;
+        constexpr uint32_t LINE = 128 / sizeof(T);
+        const uint32_t ft = blockIdx.x + (uint32_t)pf;
+        if (pf <= 0 || ft >= gridDim.x) return;
+        // lines per population range: one more than whole lines, for a range
+        // that does not start on a line boundary
+        const uint32_t per = (blockDim.x + LINE - 1) / LINE + 1;
+        const uint32_t t = threadIdx.x;
+        if (t >= V::Q * per + 2) return;
+        const EnsMember<R>& F = members[__ldg(tile_member + ft)];
+        const uint32_t n0 = (ft - F.tile0) * blockDim.x;
+        const uint32_t last = min(blockDim.x, F.ncells - n0) - 1;   // tile ft holds cells n0 .. n0 + last
+        if (t < V::Q * per) {
+            const uint32_t i = t / per, k = t - i * per;
+            const T* src = (const T*)F.args[parity].src + (size_t)i * F.ncells + n0;
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(src + min(k * LINE, last)));
+        } else if (F.args[parity].flags) {
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(F.args[parity].flags + n0 + min((t - V::Q * per) * 128u, last)));
+        }
+    }
+}
+
 // The plain cells (flag byte 0) of every member; the others come from the
 // ensemble's list (k_ensemble_list).
 template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
+    prefetch_tile_ahead<V, FMT>(members, tile_member, parity, M.args[parity].pf);
     const uint32_t n = (blockIdx.x - M.tile0) * blockDim.x + threadIdx.x;
     if (n >= M.ncells) return;
     const StepArgs<R> a = M.args[parity];
@@ -830,8 +933,11 @@ __global__ void k_mark_neighbours(uint8_t* flags, int nx, int ny, int nz) {
         const Nbr nb(x, y, z, nx, ny, nz);
         uint32_t any = 0;
         static_for<1, V::Q>([&](auto I) { any |= flags[nb.up<V, I.value>()]; });
+        // only the user bits of the neighbours are read (other threads add
+        // internal bits to the bytes meanwhile)
         uint32_t add = 0;
         if ((any & F_WALL) || (fl & F_OUTFLOW)) add |= F_NEAR_SOLID;
+        if (any & F_FREESLIP) add |= F_NEAR_FREESLIP;
         if (any & F_MOVING) add |= F_NEAR_MOVING;
         if (add) flags[n] = (uint8_t)(fl | add);
     }
