@@ -205,6 +205,7 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
     mem = build()
     e = P.Ensemble(mem)
     bx, by = e.autotune(trial_steps=3)
+    scheme = e.scheme()
     e.step(warmup)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize()
@@ -223,8 +224,8 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
     for g in mem:
         g.close()
     return {"workload": f"{count} D3Q19 SRT lid-driven cavities, edges U{{16..128}} (splitmix64 seed {seed}), "
-                        f"tau U[0.51,0.9], lid U[0.02,0.1], FP32/FP16S, A-B",
-            "cells": cells, "steps": steps, "tile": [bx, by],
+                        f"tau U[0.51,0.9], lid U[0.02,0.1], FP32/FP16S, tile and streaming scheme autotuned",
+            "cells": cells, "steps": steps, "tile": [bx, by], "scheme": scheme,
             "batched_mlups": cells * steps / t_b / 1e6, "per_launch_mlups": cells * steps / t_e / 1e6,
             "speedup": t_e / t_b, "launches_per_step": {"batched": 2, "per_launch": 2 * count}}
 
