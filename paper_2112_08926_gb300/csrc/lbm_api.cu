@@ -490,8 +490,9 @@ lbm_status put_all(lbm_handle* h, const Relax<R>& k, int setf, int per_cell, Up 
         L.stream = h->stream;
         if (h->cuda(h->ks->put[(h->aa() ? 1 : 0) | (h->chunked ? 2 : 0)](&pa, setf, L), "put kernel"))
             return LBM_ERR_CUDA;
-        if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
+        // the next chunk's upload into the staging buffer follows this kernel in stream order
     }
+    if (h->cuda(cudaStreamSynchronize(h->stream), "sync")) return LBM_ERR_CUDA;
     h->t = 0;
     h->cur = 0;
     return LBM_OK;
@@ -647,9 +648,12 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
         L.block = dim3(32, 8, 1);
         L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
         L.stream = s;
-        // prefetch one plane beyond the planes the resident blocks (3 per SM) cover
-        const long per_plane = (long)L.grid.x * L.grid.y, resident = 3L * h->num_sms;
-        a.pf = (int)std::min<long>(8, (resident + per_plane - 1) / per_plane + 1);
+        // prefetch distance: about one and a half waves of blocks (3 resident
+        // per SM), as rows of 8 (one block row) split into planes and rows
+        const long ahead = 3L * h->num_sms * 3 / 2;
+        const long rows = (ahead + L.grid.x - 1) / L.grid.x * 8;
+        a.pf = (int)(rows / h->p.ny);
+        a.pf_y = (int)(rows % h->p.ny);
         st = h->cuda(h->ks->pair_chunked[scheme][h->flags ? 1 : 0](&a, L), "chunked step kernel");
         // the non-plain cells; the paired kernel updates the plain bounce-back
         // cells itself except in the odd A-A half
@@ -732,7 +736,7 @@ lbm_status probe_chunks(lbm_handle* h, const Relax<R>& k, int mode, int per_cell
         lbm_status st = download(z0, z1, count);
         if (st != LBM_OK) return st;
     }
-    return LBM_OK;
+    return h->cuda(cudaStreamSynchronize(h->stream), "sync");
 }
 
 }  // namespace
@@ -749,7 +753,7 @@ extern "C" lbm_status lbm_get_rho_u(lbm_handle* h, double* rho, double* ux, doub
             if (dst[c] && h->cuda(cudaMemcpyAsync(dst[c] + off, h->scratch + c * count, count * sizeof(double),
                                                   cudaMemcpyDeviceToHost, h->stream), "fields download"))
                 return LBM_ERR_CUDA;
-        return h->cuda(cudaStreamSynchronize(h->stream), "sync");
+        return LBM_OK;   // the next chunk's probe follows these copies in stream order
     };
     st = h->fp64() ? probe_chunks(h, h->kd, PROBE_FIELDS, 4, download)
                    : probe_chunks(h, h->kf, PROBE_FIELDS, 4, download);
@@ -768,7 +772,7 @@ extern "C" lbm_status lbm_get_f(lbm_handle* h, double* f) {
             if (h->cuda(cudaMemcpyAsync(f + (size_t)i * h->N + off, h->scratch + i * count, count * sizeof(double),
                                         cudaMemcpyDeviceToHost, h->stream), "f download"))
                 return LBM_ERR_CUDA;
-        return h->cuda(cudaStreamSynchronize(h->stream), "sync");
+        return LBM_OK;   // the next chunk's probe follows these copies in stream order
     };
     st = h->fp64() ? probe_chunks(h, h->kd, PROBE_F, h->q, download)
                    : probe_chunks(h, h->kf, PROBE_F, h->q, download);

@@ -59,6 +59,7 @@ template <class R> struct StepArgs {
     uint32_t N;
     Relax<R> k;
     int pf;                   // L2 prefetch distance: z-planes (chunked kernels), tiles (ensemble); 0: none
+    int pf_y;                 // chunked kernels: further rows of the prefetch distance (< ny)
 };
 
 struct Nbr {
@@ -571,16 +572,18 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
     uint16_t* dst = (uint16_t*)a.dst;
     const uint32_t own_chunk = (ry[1] + rz[1]) * XT + X;   // < 2^25: N < 2^31 cells
     // Blocks start in launch order (x, then y, then z), so the warp at the
-    // same chunk and row pf planes further runs about one wave later: this
-    // warp sends its q lines (and, flagged, its flag line) into L2 ahead of
-    // it.  Nothing waits on these prefetches, so they keep HBM busy beyond
-    // the loads the registers of the resident warps can hold; the bytes read
-    // from HBM stay the same.  Only the formats with hardware conversion are
-    // bound by HBM; the others are bound by instruction issue and skip it.
+    // same chunk a.pf planes and a.pf_y rows further runs about one wave
+    // later: this warp sends that row's q lines (and, flagged, its flag
+    // line) into L2 ahead of it.  Nothing waits on these prefetches, so they
+    // keep HBM busy beyond the loads the registers of the resident warps can
+    // hold; the bytes read from HBM stay the same.  Only the formats with
+    // hardware conversion are bound by HBM; the others are bound by
+    // instruction issue and skip it.
     if constexpr (FMT == 2 || FMT == 3) {
-        const int zf = z + a.pf;
-        if (a.pf > 0 && zf < a.nz) {
-            const uint32_t fut = (ry[1] + (uint32_t)zf * ny) * XT + X;
+        int yf = y + a.pf_y, zf = z + a.pf;
+        if (yf >= a.ny) { yf -= a.ny; ++zf; }
+        if ((a.pf > 0 || a.pf_y > 0) && zf < a.nz) {
+            const uint32_t fut = ((uint32_t)yf + (uint32_t)zf * ny) * XT + X;
             if (lane < V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)fut * CHE + lane * CHUNK));
             else if (PLAIN && lane == V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(a.flags + (size_t)fut * CHUNK));
         }
