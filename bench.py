@@ -485,14 +485,18 @@ def main():
     outs = [torch.empty(N, dtype=torch.float64).pin_memory() for _ in range(4)]
     g.set_rho_u_ptr(*[p.data_ptr() for p in pin])
     g.step(args.warmup)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    g.set_rho_u_ptr(*[p.data_ptr() for p in pin])
-    g.step(args.steps)
     g.get_rho_u_ptr(*[o.data_ptr() for o in outs])
-    torch.cuda.synchronize()
-    e2e_t = time.perf_counter() - t0
-    e2e_t = max_over_ranks(dist, e2e_t, "cuda")
+    # the whole job (upload, K steps, readback) three times; the median job time
+    jobs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_rho_u_ptr(*[p.data_ptr() for p in pin])
+        g.step(args.steps)
+        g.get_rho_u_ptr(*[o.data_ptr() for o in outs])
+        torch.cuda.synchronize()
+        jobs.append(time.perf_counter() - t0)
+    e2e_t = max_over_ranks(dist, sorted(jobs)[1], "cuda")
     g.close()
     e2e = {"value": job_mlups(world, N, args.steps, e2e_t), "unit": "MLUPs/s",
            "h2d_bytes_per_step": 4 * N * 8 / args.steps, "d2h_bytes_per_step": 4 * N * 8 / args.steps}
