@@ -235,6 +235,10 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
 extern "C" lbm_status lbm_destroy(lbm_handle* h) {
     if (!h) return LBM_OK;
     cudaStreamSynchronize(h->stream);
+    for (auto& row : h->graph)
+        for (auto& g : row)
+            if (g) cudaGraphExecDestroy(g);
+    if (h->capture) cudaStreamDestroy(h->capture);
     for (void* ptr : h->allocations) h->al.release(ptr, h->al.ctx);
     h->allocations.clear();
     delete h;
@@ -244,6 +248,7 @@ extern "C" lbm_status lbm_destroy(lbm_handle* h) {
 extern "C" lbm_status lbm_set_block(lbm_handle* h, int bx, int by) {
     if (!h) return LBM_ERR_ARG;
     if (bx < 1 || by < 1 || bx * by > 256 || (bx * by) % 32 != 0) return h->fail(LBM_ERR_ARG, "block shape");
+    ++h->gen;
     h->bx = bx;
     h->by = by;
     return LBM_OK;
@@ -299,6 +304,7 @@ __global__ void k_scatter_nodes(const int64_t* cells, uint32_t m, const float* u
 extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, const float* node_u, const float* node_rho) {
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
+    ++h->gen;
     const size_t N = h->N;
     if (!flags) {
         h->has_open_boundaries = false;
@@ -414,6 +420,7 @@ extern "C" lbm_status lbm_set_nodes(lbm_handle* h, int64_t count, const int64_t*
                                     const float* node_rho) {
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
+    ++h->gen;
     if (!h->flags) return h->fail(LBM_ERR_ARG, "lbm_set_nodes needs flags (call lbm_set_geometry first)");
     if ((st = check_cell_list(h, count, cells)) != LBM_OK) return st;
     {
@@ -470,6 +477,7 @@ namespace {
 template <class R, class Up>
 lbm_status put_all(lbm_handle* h, const Relax<R>& k, int setf, int per_cell, Up upload) {
     const size_t fbytes = (size_t)h->q * h->N * h->sb;
+    ++h->gen;
     for (int c = 0; c < (h->aa() ? 1 : 2); ++c)
         if (h->cuda(cudaMemsetAsync(h->f[c], 0, fbytes, h->stream), "memset")) return LBM_ERR_CUDA;
     h->chunked = want_chunked(h) ? 1 : 0;   // the populations are rewritten: take the best layout
@@ -618,6 +626,7 @@ lbm_status zero_solid(lbm_handle* h) {
 lbm_status ensure_layout(lbm_handle* h) {
     const int want = want_chunked(h) ? 1 : 0;
     if (want == h->chunked) return LBM_OK;
+    ++h->gen;
     // A-B: into the other copy; A-A (one copy): through a transient copy of it
     const size_t fbytes = (size_t)h->q * h->N * h->sb;
     TempBuffer tmp(h, h->aa() ? fbytes : 0);
@@ -702,11 +711,77 @@ lbm_status lbm_internal_step(lbm_handle* h, cudaStream_t s) {
     return h->fp64() ? launch_one_step(h, h->kd, s) : launch_one_step(h, h->kf, s);
 }
 
+namespace {
+
+// Lattices up to kGraphCells cells, whose steps are short enough for launch
+// overhead to show, replay runs of kStepGraph steps from a CUDA graph.
+constexpr int kStepGraph = 32;                       // even: cur and t & 1 return to their start values
+constexpr size_t kGraphCells = size_t(1) << 23;
+
+// the graph of kStepGraph steps from the current state, captured if missing
+// or stale; *out stays NULL where the runtime declines the capture
+lbm_status step_graph(lbm_handle* h, cudaGraphExec_t* out) {
+    *out = nullptr;
+    const int c = h->cur, par = (int)(h->t & 1);
+    if (h->graph[c][par] && h->graph_gen[c][par] == h->gen) {
+        *out = h->graph[c][par];
+        return LBM_OK;
+    }
+    if (h->graph[c][par]) {
+        if (h->cuda(cudaGraphExecDestroy(h->graph[c][par]), "graph destroy")) return LBM_ERR_CUDA;
+        h->graph[c][par] = nullptr;
+    }
+    if (!h->capture && h->cuda(cudaStreamCreateWithFlags(&h->capture, cudaStreamNonBlocking), "capture stream"))
+        return LBM_ERR_CUDA;
+    // capture on the private stream (nothing runs); the replays go to h->stream.
+    // A capture the runtime refuses leaves the steps to plain launches.
+    if (cudaStreamBeginCapture(h->capture, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_OK;
+    }
+    const int64_t t0 = h->t;
+    const int c0 = h->cur;
+    lbm_status st = LBM_OK;
+    for (int k = 0; k < kStepGraph && st == LBM_OK; ++k) st = lbm_internal_step(h, h->capture);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(h->capture, &graph);
+    h->t = t0;
+    h->cur = c0;
+    if (st != LBM_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (st != LBM_OK) return st;   // a launch failed: reported like an uncaptured one
+        cudaGetLastError();
+        return LBM_OK;
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e2 != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_OK;
+    }
+    h->graph[c][par] = exec;
+    h->graph_gen[c][par] = h->gen;
+    *out = exec;
+    return LBM_OK;
+}
+
+}  // namespace
+
 extern "C" lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
     if (nsteps < 0) return h->fail(LBM_ERR_ARG, "negative step count");
-    for (int64_t s = 0; s < nsteps; ++s) {
+    int64_t s = 0;
+    if (h->N <= kGraphCells && nsteps >= 2 * kStepGraph) {
+        cudaGraphExec_t g = nullptr;
+        if ((st = step_graph(h, &g)) != LBM_OK) return st;
+        for (; g && s + kStepGraph <= nsteps; s += kStepGraph) {
+            if (h->cuda(cudaGraphLaunch(g, h->stream), "graph launch")) return LBM_ERR_CUDA;
+            h->t += kStepGraph;   // h->cur is back at its start value
+        }
+    }
+    for (; s < nsteps; ++s) {
         st = lbm_internal_step(h, h->stream);
         if (st != LBM_OK) return st;
     }
@@ -945,6 +1020,7 @@ extern "C" lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx_out, 
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
     if (trial_steps < 1) return h->fail(LBM_ERR_ARG, "trial_steps < 1");
+    ++h->gen;
     static const int shapes[][2] = {{128, 2}, {256, 1}, {64, 4}, {32, 8}, {64, 2}, {128, 1}, {32, 4}};
     cudaEvent_t ev[2];
     if (h->cuda(cudaEventCreate(&ev[0]), "event") || h->cuda(cudaEventCreate(&ev[1]), "event")) return LBM_ERR_CUDA;
@@ -1024,12 +1100,14 @@ extern "C" lbm_status lbm_set_scheme(lbm_handle* h, int scheme) {
     }
     h->cur = 0;
     h->p.scheme = scheme;
+    ++h->gen;
     return ensure_layout(h);
 }
 
 extern "C" lbm_status lbm_set_variant(lbm_handle* h, int variant) {
     if (!h) return LBM_ERR_ARG;
     if (variant < LBM_VARIANT_AUTO || variant > LBM_VARIANT_PAIRED) return h->fail(LBM_ERR_ARG, "variant");
+    ++h->gen;
     h->variant = variant;
     return ensure_layout(h);
 }

@@ -48,6 +48,14 @@ struct lbm_handle {
     Relax<double> kd{};
     size_t device_bytes = 0;
     std::vector<void*> allocations;
+    // CUDA graphs of kStepGraph consecutive steps, by (cur, t & 1) at their
+    // start, captured on a private stream and replayed on `stream`; a graph
+    // is valid while `gen` (bumped by every call that changes what a step
+    // launches) equals the value it was captured at
+    uint64_t gen = 0;
+    cudaStream_t capture = nullptr;
+    cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    uint64_t graph_gen[2][2] = {{0, 0}, {0, 0}};
 
     bool aa() const { return p.scheme == LBM_STREAM_AA; }
     // every population element index fits in 32 bits

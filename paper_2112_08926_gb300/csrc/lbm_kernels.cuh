@@ -279,10 +279,12 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
 }
 
 // IX: element-index type, uint32_t when q*N < 2^32 (cheaper address arithmetic).
+// MRT's two 19 x 19 transforms need about 80 registers: 3 blocks per SM
+// instead of 4 keep them without spills.
 // FLAGS: the lattice has flags; then this kernel updates the plain cells
 // (flag byte 0) only and k_step_list the listed others.
 template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
-__global__ void __launch_bounds__(256, (sizeof(R) == 8 || (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8)) ? 2 : 4)
+__global__ void __launch_bounds__(256, (sizeof(R) == 8 || (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8)) ? 2 : (COLL == 2 ? 3 : 4))
     k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -755,7 +757,7 @@ __device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restri
 // The plain cells (flag byte 0) of every member; the others come from the
 // ensemble's list (k_ensemble_list).
 template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
-__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k_ensemble_step(const EnsMember<R>* __restrict__ members,
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : (COLL == 2 ? 3 : 4)) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
     prefetch_tile_ahead<V, FMT>(members, tile_member, parity, M.args[parity].pf);

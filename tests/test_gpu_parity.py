@@ -437,6 +437,50 @@ def test_plain_bounce_back_cells_in_fast_kernels(vs, shape, scheme, storage):
     g.close()
 
 
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+@pytest.mark.parametrize("storage", ["FP32", "FP16S"])
+def test_graph_replayed_steps_bitwise(scheme, storage):
+    """Calls of 64 steps or more on lattices up to 2^23 cells replay runs of
+    32 steps from a CUDA graph: bit-equal to one launch per step and to the
+    oracle, from either step parity (the graphs are keyed by it) and after
+    calls that change what a step launches (kernel variant, geometry)."""
+    nz, ny, nx = 5, 9, 64
+    shape = (nz, ny, nx)
+    fields = W.random_fields(shape, 71)
+    extra = {"outflow": 0.0, "freeslip_frac": 0.0} if scheme == "AA" else {}
+    geo = W.random_geometry(shape, 72, **extra)
+
+    def make():
+        g = P().Lattice(nx, ny, nz, "D3Q19", "SRT", storage, "FP32", scheme, tau=0.7)
+        g.set_geometry(*geo)
+        g.set_rho_u(*fields)
+        return g
+
+    a, b = make(), make()
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "SRT", "ORD32", storage, tau=0.7)
+    o.set_geometry(*geo)
+    o.set_rho_u(*fields)
+    a.step(101)                      # three replays and five launches
+    for _ in range(101):
+        b.step(1)
+    o.step(101)
+    assert np.array_equal(a.f(), b.f())
+    assert np.array_equal(a.f(), o.f())
+    a.step(64)                       # odd start: the graph of the other parity
+    o.step(64)
+    assert np.array_equal(a.f(), o.f())
+    a.set_variant("generic")         # another kernel: the graphs are captured again
+    a.step(65)
+    o.step(65)
+    assert np.array_equal(a.f(), o.f())
+    a.set_geometry(*geo)             # a new cell list
+    a.step(66)
+    o.step(66)
+    assert np.array_equal(a.f(), o.f())
+    a.close()
+    b.close()
+
+
 def test_d3q27_stays_generic():
     g = P().Lattice(64, 3, 2, "D3Q27", "SRT", "FP16S", "FP32", "AB", tau=0.7)
     g.set_variant("paired")
