@@ -204,10 +204,11 @@ lbm_status lbm_set_f(lbm_handle* h, const double* f);
 lbm_status lbm_reduce(lbm_handle* h, double* mass, double* kinetic_energy);
 
 /* memory layout of the populations: structure of arrays f[i*N + n], or the
- * chunked layout of flag-free A-B lattices with 16-bit storage and nx a
- * multiple of 64 (chosen by LBM_VARIANT_AUTO / _PAIRED): the cells of each
- * row are cut into chunks of 64, and chunk c = n/64 holds its q populations
- * one after the other, element ((n/64)*q + i)*64 + n%64. */
+ * chunked layout of lattices with 16-bit storage, FP32 arithmetic and nx a
+ * multiple of 64 (A-B or A-A, with or without flags; D3Q27 only with FP16 or
+ * FP16S; chosen by LBM_VARIANT_AUTO / _PAIRED): the cells of each row are
+ * cut into chunks of 64, and chunk c = n/64 holds its q populations one
+ * after the other, element ((n/64)*q + i)*64 + n%64. */
 enum { LBM_LAYOUT_SOA = 0, LBM_LAYOUT_CHUNKED = 1 };
 
 typedef struct {
@@ -230,11 +231,13 @@ lbm_status lbm_set_block(lbm_handle* h, int bx, int by);
 /* Stream-collide kernel variants; all give bit-for-bit the same result.
  *   GENERIC  one cell per thread, every lattice and boundary kind;
  *   PAIRED   two x-neighbouring cells per thread, populations moved as
- *            32-bit pairs of codes (flag-free A-B lattices with 16-bit
- *            storage, FP32 arithmetic, even nx, q*N < 2^32, block width a
- *            multiple of 32); with nx a multiple of 64 it runs on the
- *            chunked layout (LBM_LAYOUT_CHUNKED), every warp moving whole
- *            128-byte lines at compile-time offsets;
+ *            32-bit pairs of codes, 16-bit storage and FP32 arithmetic:
+ *            with nx a multiple of 64 on the chunked layout
+ *            (LBM_LAYOUT_CHUNKED; A-B or A-A, with or without flags),
+ *            every warp moving whole 128-byte lines at compile-time
+ *            offsets; otherwise on the structure-of-arrays layout for
+ *            flag-free A-B lattices with even nx, q*N < 2^32 and a block
+ *            width that is a multiple of 32;
  *   STAGED   source rows prefetched into shared memory by bulk copies
  *            several tiles ahead (flag-free A-B D3Q19 lattices, FP32
  *            arithmetic, nx of 128, 256 or 512); a copy wait that runs out

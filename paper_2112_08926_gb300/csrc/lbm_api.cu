@@ -658,8 +658,9 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
         L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
         L.stream = s;
         // prefetch distance: about one and a half waves of blocks (3 resident
-        // per SM), as rows of 8 (one block row) split into planes and rows
-        const long ahead = 3L * h->num_sms * 3 / 2;
+        // per SM, 2 for D3Q27), as rows of 8 (one block row) split into planes
+        // and rows
+        const long ahead = (h->q > 19 ? 2L : 3L) * h->num_sms * 3 / 2;
         const long rows = (ahead + L.grid.x - 1) / L.grid.x * 8;
         a.pf = (int)(rows / h->p.ny);
         a.pf_y = (int)(rows % h->p.ny);

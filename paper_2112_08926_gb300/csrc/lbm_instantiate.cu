@@ -114,17 +114,19 @@ void fill() {
     s.put[0] = launch_put<V, 0>;
     s.put[1] = launch_put<V, 1>;
     // the chunked layout and the paired kernels: 16-bit storage, FP32
-    // arithmetic; D3Q27 keeps the generic kernels (27 code pairs per lane do
-    // not fit the register budget of the paired kernels)
-    // MRT keeps the generic kernels too (its 19 x 19 transforms per cell pair
+    // arithmetic; D3Q27 only with the hardware conversions (FP16, FP16S: the
+    // software codecs are bound by instruction issue, and the paired kernel
+    // takes D3Q27's two cells one after the other to fit 27 code pairs)
+    // MRT keeps the generic kernels (its 19 x 19 transforms per cell pair
     // would double the build for a kernel the operator cannot keep fed)
-    if constexpr (LBM_ARITH == 0 && FMT >= 2 && COLL < 2 && !std::is_same<V, D3Q27>::value) {
+    if constexpr (LBM_ARITH == 0 && FMT >= 2 && COLL < 2 &&
+                  (!std::is_same<V, D3Q27>::value || FMT == 2 || FMT == 3)) {
         s.probe[LAYOUT_AB_CHUNKED] = launch_probe<V, LAYOUT_AB_CHUNKED>;
         s.probe[LAYOUT_AA_SWAPPED_CHUNKED] = launch_probe<V, LAYOUT_AA_SWAPPED_CHUNKED>;
         s.probe[LAYOUT_AA_NATURAL_CHUNKED] = launch_probe<V, LAYOUT_AA_NATURAL_CHUNKED>;
         s.put[2] = launch_put<V, 2>;
         s.put[3] = launch_put<V, 3>;
-        s.pair = launch_pair<V, COLL>;
+        if constexpr (!std::is_same<V, D3Q27>::value) s.pair = launch_pair<V, COLL>;   // SoA paired: up to q = 19
         static_for<0, 3>([&](auto PH) {
             s.pair_chunked[PH.value][0] = launch_pair_chunked<V, COLL, PH.value, false>;
             s.pair_chunked[PH.value][1] = launch_pair_chunked<V, COLL, PH.value, true>;

@@ -554,7 +554,7 @@ template <> struct PairCodec<3> : PairCodecHalf<3> {};
 // F_NEAR_SOLID); a pair with one such cell is written as a single 16-bit
 // code; the other cells belong to the list kernel.
 template <class V, int COLL, int FMT, int PHASE, bool PLAIN>
-__global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<float> a) {
+__global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(const StepArgs<float> a) {
     using PC = PairCodec<FMT>;
     constexpr int SL = Codec16<FMT>::SL;
     constexpr uint32_t CHE = (uint32_t)V::Q * CHUNK;     // codes per chunk
@@ -659,11 +659,32 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
             }
         }
     }
-    float fa[V::Q], fb[V::Q];
+    // SEQ (27 populations): one cell at a time, the first cell's codes going
+    // back into g before the second is decoded, so that only one cell's
+    // values are live (the register budget of 27 code pairs); otherwise both
+    // cells are decoded and encoded as pairs
+    constexpr bool SEQ = V::Q > 19;
+    float fa[V::Q], fb[SEQ ? 1 : V::Q];
     static_for<0, V::Q>([&](auto I) { fa[I.value] = PC::dec(g[I.value]).x; });
     collide<V, COLL, float, SL>(a.k, fa);
-    static_for<0, V::Q>([&](auto I) { fb[I.value] = PC::dec(g[I.value]).y; });
-    collide<V, COLL, float, SL>(a.k, fb);
+    if constexpr (SEQ) {
+        static_for<0, V::Q>([&](auto I) {
+            g[I.value] = (g[I.value] & 0xFFFF0000u) | Codec16<FMT>::enc_g(fa[I.value]);
+            fa[I.value] = PC::dec(g[I.value]).y;
+        });
+        collide<V, COLL, float, SL>(a.k, fa);
+        static_for<0, V::Q>([&](auto I) {
+            g[I.value] = (g[I.value] & 0xFFFFu) | (Codec16<FMT>::enc_g(fa[I.value]) << 16);
+        });
+    } else {
+        static_for<0, V::Q>([&](auto I) { fb[I.value] = PC::dec(g[I.value]).y; });
+        collide<V, COLL, float, SL>(a.k, fb);
+    }
+    // the new code pair of population i
+    auto pair = [&](auto I) -> uint32_t {
+        if constexpr (SEQ) return g[I.value];
+        else return PC::enc(fa[I.value], fb[I.value]);
+    };
     // writes the pair w of 16-bit codes at element e (of line start `line`),
     // only the halves whose cells may be written (ok bit 0: lo, bit 1: hi)
     auto put = [&](uint16_t* line, int e, uint32_t w, uint32_t ok) {
@@ -675,7 +696,7 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
         uint16_t* out = dst + (size_t)own_chunk * CHE + 2 * lane;
         static_for<0, V::Q>([&](auto I) {
             constexpr int slot = PHASE == LAYOUT_AA_NATURAL ? opposite(I.value) : I.value;
-            const uint32_t w = PC::enc(fa[I.value], fb[I.value]);
+            const uint32_t w = pair(I);
             if constexpr (PLAIN) put(out + slot * CHUNK, 0, w, pl);
             else *reinterpret_cast<uint32_t*>(out + slot * CHUNK) = w;
         });
@@ -685,7 +706,7 @@ __global__ void __launch_bounds__(256, 3) k_step_pair_chunked(const StepArgs<flo
         static_for<0, V::Q>([&](auto I) {
             constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
             uint16_t* rowp = dst + (size_t)((ry[1 + cy] + rz[1 + cz]) * XT + X) * CHE + i * CHUNK;
-            const uint32_t own = PC::enc(fa[i], fb[i]);
+            const uint32_t own = pair(I);
             if constexpr (cx == 0) {
                 if constexpr (PLAIN) put(rowp, 2 * lane, own, pl);
                 else *reinterpret_cast<uint32_t*>(rowp + 2 * lane) = own;

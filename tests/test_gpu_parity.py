@@ -372,7 +372,7 @@ def test_chunked_layout_every_scheme_bitwise(vs, scheme, geo_kind, storage):
     """16-bit lattices with nx a multiple of 64 run on the chunked layout with
     the paired kernels, for A-B and both A-A halves, flag-free or with a
     random geometry (plain cells paired, boundary cells from the list).
-    D3Q27 keeps the generic kernels (see test_d3q27_stays_generic)."""
+    D3Q27 has its own test (test_d3q27_chunked_bitwise)."""
     nz, ny, nx = CH_SHAPES[vs]
     shape = (nz, ny, nx)
     fields = W.random_fields(shape, 51)
@@ -481,10 +481,41 @@ def test_graph_replayed_steps_bitwise(scheme, storage):
     b.close()
 
 
-def test_d3q27_stays_generic():
-    g = P().Lattice(64, 3, 2, "D3Q27", "SRT", "FP16S", "FP32", "AB", tau=0.7)
+def test_d3q27_software_codecs_stay_generic():
+    """D3Q27 takes the chunked paired kernel only with the hardware
+    conversions (FP16, FP16S); the software codecs keep the generic kernel."""
+    g = P().Lattice(64, 3, 2, "D3Q27", "SRT", "FP16C", "FP32", "AB", tau=0.7)
     g.set_variant("paired")
     assert g.variant() == "generic" and g.info().layout == 0
+    g.close()
+
+
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+@pytest.mark.parametrize("geo_kind", ["free", "flags"])
+@pytest.mark.parametrize("storage,coll", [("FP16S", "TRT"), ("FP16", "SRT")])
+def test_d3q27_chunked_bitwise(scheme, geo_kind, storage, coll):
+    """D3Q27 on the chunked layout: the paired kernel takes a lane's two
+    cells one after the other (27 code pairs); bit-equal to the oracle for
+    A-B and both A-A halves, flag-free or with a random geometry."""
+    nz, ny, nx = 3, 5, 128
+    shape = (nz, ny, nx)
+    fields = W.random_fields(shape, 81)
+    force = FORCE["D3Q27"]
+    g = P().Lattice(nx, ny, nz, "D3Q27", coll, storage, "FP32", scheme, tau=0.66, trt_lambda=0.2, force=force)
+    o = oracle.Lattice(nx, ny, nz, "D3Q27", coll, "ORD32", storage, tau=0.66, trt_lambda=0.2, force=force)
+    if geo_kind == "flags":
+        extra = {"outflow": 0.0, "freeslip_frac": 0.0} if scheme == "AA" else {}
+        geo = W.random_geometry(shape, 82, **extra)
+        g.set_geometry(*geo)
+        o.set_geometry(*geo)
+    g.set_rho_u(*fields)
+    o.set_rho_u(*fields)
+    assert g.info().layout == 1 and g.variant() == "paired"
+    g.step(21)
+    o.step(21)
+    assert np.array_equal(g.f(), o.f())
+    for a, b in zip(g.rho_u(), o.rho_u()):
+        assert np.array_equal(a, b)
     g.close()
 
 
