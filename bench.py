@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -184,7 +185,58 @@ def cpu_baseline(n, storage, budget_s=10.0):
     dt = time.perf_counter() - t0
     return {"value": n ** 3 * k / dt / 1e6, "unit": "MLUPs/s", "cores": oracle.threads(), "kind": "oracle",
             "sample": f"{k} oracle steps (after 1 warm-up) of the same D3Q19 SRT TGV {n}^3 lattice, "
-                      f"FP32 ordered arithmetic with {storage} storage"}
+                      f"FP32 ordered arithmetic with {storage} storage",
+            "cpu_model": cpu_model(), "one_core": oracle_one_core(storage=storage)}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu), else its architecture."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def oracle_one_core(n=64, storage="FP16S", budget_s=2.0):
+    """The same oracle step on one thread, on an n^3 sample of the workload."""
+    import oracle
+    import workloads as W
+    threads = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        o = oracle.Lattice(n, n, n, "D3Q19", "SRT", "ORD32", storage, tau=0.53)
+        o.set_rho_u(*W.taylor_green_extruded(n, 0.05))
+        t0 = time.perf_counter()
+        o.step(1)
+        k = max(1, min(50, int(budget_s / max(time.perf_counter() - t0, 1e-6))))
+        t0 = time.perf_counter()
+        o.step(k)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(threads)
+    return {"value": n ** 3 * k / dt / 1e6, "unit": "MLUPs/s", "cores": 1,
+            "sample": f"{k} oracle steps of a {n}^3 D3Q19 SRT TGV lattice, FP32 ordered arithmetic, {storage} storage"}
+
+
+def oracle_cavity(n, storage, tau, u_lid, budget_s=4.0):
+    """The oracle on the same cavity (all host cores): MLUPs/s over a few steps."""
+    import oracle
+    import workloads as W
+    o = oracle.Lattice(n, n, n, "D3Q19", "TRT", "ORD32", storage, tau=tau)
+    flags, node_u = W.cavity(n, u_lid)
+    o.set_geometry(flags, node_u)
+    o.set_rho_u()
+    t0 = time.perf_counter()
+    o.step(1)
+    k = max(1, min(20, int(budget_s / max(time.perf_counter() - t0, 1e-6))))
+    t0 = time.perf_counter()
+    o.step(k)
+    dt = time.perf_counter() - t0
+    return {"value": n ** 3 * k / dt / 1e6, "cores": oracle.threads(), "steps": k}
 
 
 def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
@@ -230,11 +282,14 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
             "speedup": t_e / t_b, "launches_per_step": {"batched": 2, "per_launch": 2 * count}}
 
 
-def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1, only=None):
+def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1, only=None,
+                 with_oracle=True):
     """D3Q19 TRT lid-driven cavities N^3 (wall shell included, lid z = N-1
     moving along +y, rho = 1, u = 0 at start, tau from Re = u_lid (N-2) / nu):
     FP32 storage up to 512^3, 16-bit up to 1024^3 (A-B below 768^3, in-place
-    A-A from 768^3 on).  Algorithmic bytes per cell: 2 q s + 1 (own flag)."""
+    A-A from 768^3 on).  Algorithmic bytes per cell: 2 q s + 1 (own flag).
+    At 128^3 and 256^3 the oracle's rate on the same cavity (all host cores,
+    a few steps) is reported beside the GPU's."""
     import workloads as W
     peak, _ = peaks()
     rows = []
@@ -260,6 +315,8 @@ def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0,
                          "mlups": cells * steps / dt / 1e6, "gbs": b * cells * steps / dt / 1e9,
                          "frac_hbm": b * cells * steps / dt / 1e9 / peak, "bytes_per_cell": b,
                          "device_gb": info.device_bytes / 1e9, "kinetic_energy": e})
+            if with_oracle and n in (128, 256) and storage != "FP64":
+                rows[-1]["oracle"] = oracle_cavity(n, storage, tau, u_lid)
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
     return rows
 

@@ -98,6 +98,7 @@ def lib() -> ctypes.CDLL:
             L.orc_equilibrium.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, P]
             L.orc_threads.restype = ctypes.c_int
+            L.orc_set_threads.argtypes = [ctypes.c_int]
             _lib = L
     return _lib
 
@@ -158,6 +159,12 @@ def mrt_rates(tau: float) -> np.ndarray:
 
 def threads() -> int:
     return lib().orc_threads()
+
+
+def set_threads(n: int) -> None:
+    """Threads of the following oracle calls (for timing; results do not
+    depend on the thread count)."""
+    lib().orc_set_threads(int(n))
 
 
 # ---------------------------------------------------------------- lattice

@@ -113,6 +113,8 @@ void orc_mrt_rates(double tau, double* s);
 /* shifted equilibrium of one cell in the given arithmetic mode (q values) */
 void orc_equilibrium(int velset, int arith, double rho, double ux, double uy, double uz, double* feq);
 int  orc_threads(void);
+/* threads of the following oracle calls (timing only; results do not depend on it) */
+void orc_set_threads(int n);
 
 #ifdef __cplusplus
 }

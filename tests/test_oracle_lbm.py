@@ -427,3 +427,25 @@ def test_mrt_poiseuille_curvature():
     a = np.polyfit(y, ux, 2)[0]
     nu = (tau - 0.5) / 3
     assert abs(2 * a / (-F / nu) - 1) < 1e-6
+
+
+def test_oracle_result_does_not_depend_on_thread_count():
+    """The parallel loops are over independent cells: one thread and all
+    threads give the same populations bit for bit (the timing legs of the
+    benchmark change the thread count)."""
+    shape = (4, 5, 6)
+    fields = W.random_fields(shape, 91)
+    geo = W.random_geometry(shape, 92)
+    out = []
+    n0 = oracle.threads()
+    try:
+        for t in (1, n0):
+            oracle.set_threads(t)
+            o = oracle.Lattice(6, 5, 4, "D3Q19", "TRT", "ORD32", "FP16S", tau=0.7)
+            o.set_geometry(*geo)
+            o.set_rho_u(*fields)
+            o.step(7)
+            out.append(o.f())
+    finally:
+        oracle.set_threads(n0)
+    assert np.array_equal(out[0], out[1])
