@@ -261,8 +261,15 @@ int lbm_get_variant(const lbm_handle* h);
  * LBM_ERR_UNSUPPORTED for A-A with OUTFLOW or FREESLIP cells, LBM_ERR_OOM. */
 lbm_status lbm_set_scheme(lbm_handle* h, int scheme);
 
-/* Same search as lbm_ensemble_autotune for one lattice; the trial steps
- * advance the lattice. */
+/* Times, over trial_steps steps each, the stream-collide kernel variants
+ * that apply to the lattice -- GENERIC on the structure-of-arrays layout,
+ * PAIRED (on the chunked layout where nx is a multiple of 64), STAGED -- and
+ * keeps the fastest (its layout with it; query it with lbm_get_variant);
+ * then, for the kernels that take one (GENERIC, PAIRED on the structure of
+ * arrays), the thread-block shape, returned in *bx, *by.  Every variant and
+ * shape gives the same values; the trial steps advance the lattice.  The
+ * streaming scheme stays as it is (lbm_set_scheme switches it).  Trial runs
+ * of 64 steps or more include one CUDA-graph capture (see lbm_step). */
 lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx, int* by);
 
 /* Self-test of the failure path (the paper has no counterpart): launches

@@ -1021,28 +1021,53 @@ extern "C" lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx_out, 
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
     if (trial_steps < 1) return h->fail(LBM_ERR_ARG, "trial_steps < 1");
-    ++h->gen;
-    static const int shapes[][2] = {{128, 2}, {256, 1}, {64, 4}, {32, 8}, {64, 2}, {128, 1}, {32, 4}};
     cudaEvent_t ev[2];
     if (h->cuda(cudaEventCreate(&ev[0]), "event") || h->cuda(cudaEventCreate(&ev[1]), "event")) return LBM_ERR_CUDA;
-    float best = 1e30f;
-    int bb[2] = {h->bx, h->by};
-    for (const auto& sh : shapes) {
-        h->bx = sh[0];
-        h->by = sh[1];
-        if ((st = lbm_step(h, 2)) != LBM_OK) break;
+    // 2 untimed steps, then trial_steps timed on the lattice's stream
+    auto trial = [&](float* ms) -> lbm_status {
+        lbm_status s2 = lbm_step(h, 2);
+        if (s2 != LBM_OK) return s2;
         cudaEventRecord(ev[0], h->stream);
-        if ((st = lbm_step(h, trial_steps)) != LBM_OK) break;
+        if ((s2 = lbm_step(h, trial_steps)) != LBM_OK) return s2;
         cudaEventRecord(ev[1], h->stream);
-        if (h->cuda(cudaEventSynchronize(ev[1]), "event sync")) { st = LBM_ERR_CUDA; break; }
+        if (h->cuda(cudaEventSynchronize(ev[1]), "event sync")) return LBM_ERR_CUDA;
+        return h->cuda(cudaEventElapsedTime(ms, ev[0], ev[1]), "event time");
+    };
+    // 1. the kernel variant, and with it the layout: GENERIC on the structure
+    //    of arrays, PAIRED (chunked layout where nx is a multiple of 64),
+    //    STAGED; those that do not apply to this lattice are skipped
+    float best = 1e30f;
+    int best_v = LBM_VARIANT_GENERIC;
+    for (int v : {LBM_VARIANT_GENERIC, LBM_VARIANT_PAIRED, LBM_VARIANT_STAGED}) {
+        if ((st = lbm_set_variant(h, v)) != LBM_OK) break;
+        if (variant_in_use(h) != v) continue;
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (ms < best) { best = ms; bb[0] = sh[0]; bb[1] = sh[1]; }
+        if ((st = trial(&ms)) != LBM_OK) break;
+        if (ms < best) { best = ms; best_v = v; }
+    }
+    if (st == LBM_OK) st = lbm_set_variant(h, best_v);
+    // 2. the thread-block shape, for the kernels that take one (the generic
+    //    kernel and the paired kernel on the structure of arrays)
+    static const int shapes[][2] = {{128, 2}, {256, 1}, {64, 4}, {32, 8}, {64, 2}, {128, 1}, {32, 4}};
+    int bb[2] = {h->bx, h->by};
+    const int vu = st == LBM_OK ? variant_in_use(h) : -1;
+    if (vu == LBM_VARIANT_GENERIC || (vu == LBM_VARIANT_PAIRED && !h->chunked)) {
+        best = 1e30f;
+        for (const auto& sh : shapes) {
+            h->bx = sh[0];
+            h->by = sh[1];
+            ++h->gen;   // the launches change: no graph of another shape is replayed
+            if (variant_in_use(h) != vu) continue;   // a width the paired kernel does not take
+            float ms = 0.f;
+            if ((st = trial(&ms)) != LBM_OK) break;
+            if (ms < best) { best = ms; bb[0] = sh[0]; bb[1] = sh[1]; }
+        }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     h->bx = bb[0];
     h->by = bb[1];
+    ++h->gen;
     if (bx_out) *bx_out = bb[0];
     if (by_out) *by_out = bb[1];
     return st;

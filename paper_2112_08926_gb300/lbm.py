@@ -339,6 +339,8 @@ class Lattice:
         self._c(self._L.lbm_set_block(self._h, int(bx), int(by)))
 
     def autotune(self, trial_steps=20):
+        """Picks the kernel variant (and with it the layout) and then the block
+        shape by timing (lbm_autotune); returns (bx, by)."""
         bx, by = ctypes.c_int(), ctypes.c_int()
         self._c(self._L.lbm_autotune(self._h, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)))
         return bx.value, by.value

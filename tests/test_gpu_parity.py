@@ -182,18 +182,24 @@ def test_unsupported_geometry_for_in_place_streaming():
     assert ei.value.status == 1
 
 
-def test_autotune_keeps_results():
-    shape = (6, 13, 40)
+@pytest.mark.parametrize("nx,scheme,flags", [(40, "AA", True), (64, "AA", True), (64, "AB", False), (128, "AB", False)])
+def test_autotune_keeps_results(nx, scheme, flags):
+    """The autotuner times the kernel variants that apply (and with them the
+    layout: structure of arrays or chunked) and then block shapes; whatever
+    it keeps, the lattice's values equal those of an untuned twin."""
+    shape = (6, 13, nx)
     geo = W.random_geometry(shape, 3, outflow=0.0, freeslip_frac=0.0)
     fields = W.random_fields(shape, 4)
     res = []
     for tune in (False, True):
-        g = P().Lattice(40, 13, 6, "D3Q19", "SRT", "FP16S", "FP32", "AA", tau=0.7)
-        g.set_geometry(*geo)
+        g = P().Lattice(nx, 13, 6, "D3Q19", "SRT", "FP16S", "FP32", scheme, tau=0.7)
+        if flags:
+            g.set_geometry(*geo)
         g.set_rho_u(*fields)
         if tune:
             bx, by = g.autotune(trial_steps=2)
             assert bx * by % 32 == 0
+            assert g.variant() in ("generic", "paired", "staged")
             done = g.info().step
         else:
             done = 0
