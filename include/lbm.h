@@ -23,7 +23,9 @@
  *     -0-, 0++ 0--, +-0 -+0, +0- -0+, 0+- 0-+); D3Q27 appends +++ ---, ++-
  *     --+, +-+ -+-, -++ +--; D2Q9 is 0, +x -x +y -y, ++ --, +- -+.
  *   - Populations are stored population-major (structure of arrays,
- *     f[i*N + n]); q*N codes per copy.
+ *     f[i*N + n]) or in the chunked layout (LBM_LAYOUT_CHUNKED below); q*N
+ *     codes per copy either way.  lbm_get_f / lbm_set_f always use the
+ *     structure-of-arrays order.
  */
 #ifndef LBM_H
 #define LBM_H
