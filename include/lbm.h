@@ -285,7 +285,7 @@ lbm_status lbm_selftest_wait_timeout(lbm_handle* h);
 const char* lbm_last_error(const lbm_handle* h);
 const char* lbm_status_string(lbm_status s);
 
-/* ---- storage codecs as device-array kernels (Sec. 3, Listing 1 formats) -- */
+/* ---- storage codecs as device-array kernels (the formats of Sec. 3) ------- */
 /* x_dev: n floats, out_dev: n 16-bit codes; storage must be a 16-bit format.
  * Device pointers, asynchronous on cuda_stream. */
 lbm_status lbm_codec_encode(int storage, const float* x_dev, uint16_t* out_dev, int64_t n,
