@@ -55,16 +55,23 @@ def test_weights_sum_and_isotropy():
 
 
 @pytest.mark.parametrize("row", golden("delta_table1.txt"), ids=lambda r: r[0])
-def test_table1_delta_shifted(row):
-    """Table 1: max |f^eq-s| / rho over u_j = c c_j/|c_j| rounds up to the printed value."""
-    vs, printed = row[0], float(row[1])
+def test_table1_delta(row):
+    """Table 1: the maxima of |f^eq| / rho and |f^eq-s| / rho over the rest
+    state and u_j = c c_j/|c_j| (c = 1/sqrt(3)) round up to the printed
+    values (the oracle's equilibrium is the shifted one; f^eq = f^eq-s + w)."""
+    vs, printed, printed_s = row[0], float(row[1]), float(row[2])
     c, w = oracle.velset(vs)
-    best = 0.0
-    for j in range(1, len(w)):
-        u = c[j] / np.linalg.norm(c[j]) / math.sqrt(3)
-        best = max(best, np.abs(oracle.equilibrium(vs, "DEF64", 1.0, u)).max())
-    assert printed - 0.01 < best <= printed
-    assert math.ceil(best * 100 - 1e-9) / 100 == pytest.approx(printed)
+    best = best_s = 0.0
+    us = [np.zeros(3)] + [c[j] / np.linalg.norm(c[j]) / math.sqrt(3) for j in range(1, len(w))]
+    for u in us:
+        feq_s = oracle.equilibrium(vs, "DEF64", 1.0, u)
+        best_s = max(best_s, np.abs(feq_s).max())
+        best = max(best, np.abs(feq_s + w).max())
+    for exact, shown in ((best, printed), (best_s, printed_s)):
+        assert shown - 0.01 < exact <= shown
+        assert math.ceil(exact * 100 - 1e-9) / 100 == pytest.approx(shown)
+    # the unshifted bound comes from the rest state: the rest population w_0
+    assert best == pytest.approx(w[0], abs=1e-15)
 
 
 @pytest.mark.parametrize("vs", VELSETS)
