@@ -24,8 +24,10 @@
  * Arithmetic modes: DEF64 writes the formulas above directly in FP64.  ORD32
  * and ORD64 follow the operation order the paper prescribes in Sec. 2.2:
  * density summed in index order and 1 added last; velocity sums in
- * alternating + / - order over opposite pairs; u = (1/rho) j with one
- * reciprocal (appendix, velocity equation); the shifted equilibrium as
+ * alternating + / - order over opposite pairs; each velocity component
+ * the momentum component divided by rho (Sec. 2.2, u_x = (f1 - f2 + ...)/rho,
+ * and the fields routine of the paper's core, which divides ux, uy and uz by
+ * rho one at a time); the shifted equilibrium as
  * A*(0.5*(B^2 + C) +- B) + D with three fused multiply-adds (A = w rho,
  * B = 3 u.c_i, C = -3 u.u, D = w (rho - 1)); SRT as
  * fma(1 - omega, f, omega * f^eq).  Every other operation order used by
@@ -272,11 +274,11 @@ struct Ordered {
         }
     }
 
-    /* velocity incl. the Guo half-force, before clamping: the momentum times
-     * 1/rho, as the appendix writes u = (1/rho) sum_i c_i f_i */
+    /* velocity incl. the Guo half-force, before clamping: each momentum
+     * component (plus F_a/2, one fused multiply-add) divided by rho, one IEEE
+     * division per component, as Sec. 2.2 writes u_x = (f1 - f2 + ...)/rho */
     void velocity(R rho, const R j[3], R u[3]) const {
-        const R inv = (R)1 / rho;
-        for (int a = 0; a < 3; ++a) u[a] = (force ? fmaR((R)0.5, F[a], j[a]) : j[a]) * inv;
+        for (int a = 0; a < 3; ++a) u[a] = (force ? fmaR((R)0.5, F[a], j[a]) : j[a]) / rho;
     }
 
     /* three-FMA shifted equilibrium; returns B_p of every pair in Bp.  For

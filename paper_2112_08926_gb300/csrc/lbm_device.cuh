@@ -476,21 +476,15 @@ __device__ __forceinline__ void moments(const R* g, R& rho, R* j, R sh) {
     j[2] = jsum<V, 2, 1, true, R>(g, R(0));
 }
 
-// u = (1/rho) (j + F/2) (appendix velocity equation, Guo half-force), before
-// clamping; j is the scaled momentum
+// u_a = (j_a + F_a/2) / rho (Sec. 2.2: each momentum component divided by
+// rho, u_x = (f1 - f2 + ...)/rho; Guo half-force), before clamping: one IEEE
+// division per component.  j is the scaled momentum; its 2^-SL is exact.
 template <class R, int SL>
 __device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
-    const R inv = R(1) / rho;
-    if (k.force) {
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const R jj = SL == 0 ? j[a] : j[a] * R(Pow2<SL>::down);
-            u[a] = fmaR(R(0.5), k.F[a], jj) * inv;
-        }
-    } else {
-        const R inv_g = SL == 0 ? inv : inv * R(Pow2<SL>::down);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = j[a] * inv_g;
+    for (int a = 0; a < 3; ++a) {
+        const R jj = SL == 0 ? j[a] : j[a] * R(Pow2<SL>::down);
+        u[a] = (k.force ? fmaR(R(0.5), k.F[a], jj) : jj) / rho;
     }
 }
 

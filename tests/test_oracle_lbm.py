@@ -456,3 +456,37 @@ def test_oracle_result_does_not_depend_on_thread_count():
     finally:
         oracle.set_threads(n0)
     assert np.array_equal(out[0], out[1])
+
+
+@pytest.mark.parametrize("arith", ["ORD32", "ORD64"])
+@pytest.mark.parametrize("with_force", [False, True])
+def test_ordered_velocity_is_the_correctly_rounded_quotient(arith, with_force):
+    """Sec. 2.2 writes each velocity component as the momentum sum divided by
+    rho (u_x = (f1 - f2 + ...)/rho); the ordered modes take one IEEE division
+    per component.  A one-cell periodic lattice streams onto itself, so
+    rho and j are the sums of the populations set here.  They are chosen on a
+    coarse dyadic grid, which makes rho = sum f + 1 and j (+ F/2) exact in
+    either precision; IEEE division is then the exactly rounded quotient
+    (for FP32 operands the FP64 quotient rounded once more to FP32 is that
+    same value).  A reciprocal multiplied into j differs from it in many of
+    these cells, which the test also checks, so it tells the two apart."""
+    rng = np.random.default_rng(20211216)
+    dt = np.float32 if arith == "ORD32" else np.float64
+    n_recip_differs = 0
+    for _ in range(200):
+        F = (rng.integers(-64, 65) * 2.0 ** -14, 0.0, 0.0) if with_force else (0.0, 0.0, 0.0)
+        L = oracle.Lattice(1, 1, 1, "D3Q19", "SRT", arith, "FP32" if arith == "ORD32" else "FP64",
+                           tau=0.8, force=F)
+        f = np.zeros(19)
+        f[1:] = rng.integers(-2048, 2049, 18) * 2.0 ** -16
+        L.set_f(f)
+        rho, ux, uy, uz = (float(a.ravel()[0]) for a in L.rho_u())
+        c, _ = oracle.velset("D3Q19")
+        assert rho == 1.0 + f.sum()                       # exact on this grid
+        for a, got in enumerate((ux, uy, uz)):
+            j = float(c[:, a] @ f) + 0.5 * F[a]           # exact on this grid
+            quotient = float(dt(np.float64(j) / np.float64(rho)))
+            assert got == quotient
+            if float(dt(dt(j) * (dt(1) / dt(rho)))) != quotient:
+                n_recip_differs += 1
+    assert n_recip_differs > 10
