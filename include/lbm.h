@@ -169,16 +169,24 @@ lbm_status lbm_get_rho_u(lbm_handle* h, double* rho, double* ux, double* uy, dou
  * that must not call cudaMalloc (it blocks the device and competes with a
  * framework's memory pool), can use this entry point instead.  It writes the
  * same values, staging through one fixed array of 2^20 doubles (8 MiB) that
- * the library reserves on every GPU it is loaded on until the process exits.
- * Limit: nx*ny <= 262144 cells (four doubles per cell of one xy-plane must
- * fit); larger planes give LBM_ERR_UNSUPPORTED with the reason in
- * lbm_last_error.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress), so make it before any stream capture.  All
- * calls share the array: calls whose work overlaps on the GPU (lattices on
- * different streams read out at the same time) race and must be serialised
- * by the caller.  Every chunk is written completely before it is read, so no
- * state carries over between calls.  Host arrays as for lbm_get_rho_u;
- * synchronises the lattice's stream. */
+ * the library places on every GPU it is used on; the array stays until the
+ * process exits.  Limit: nx*ny <= 262144 cells (four doubles per cell of one
+ * xy-plane must fit); larger planes give LBM_ERR_UNSUPPORTED with the reason
+ * in lbm_last_error.
+ * Set-up: the array's device address is looked up (cudaGetSymbolAddress,
+ * which also makes the CUDA runtime place the array) when the first lattice
+ * on a device is created, with that device current, so the memory is taken
+ * before a simulation fills the GPU and before any stream capture.  If that
+ * look-up failed, this call returns LBM_ERR_UNSUPPORTED and leaves the
+ * lattice usable.  The kernels it launches are loaded at their first launch
+ * in the process, like every other kernel of the library.
+ * All calls share the array: calls whose work overlaps on the GPU (lattices
+ * on different streams read out at the same time) race and must be
+ * serialised by the caller.  Every chunk is written completely before it is
+ * read, so no state carries over between calls.  Like lbm_get_rho_u it
+ * reports LBM_ERR_TIMEOUT if a kernel of an earlier step gave up a bounded
+ * wait.  Host arrays as for lbm_get_rho_u; synchronises the lattice's
+ * stream. */
 lbm_status lbm_get_rho_u_static(lbm_handle* h, double* rho, double* ux, double* uy, double* uz);
 
 /* Streamed populations f_i(x) (shifted unless no_ddf_shifting, decoded,

@@ -216,6 +216,8 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev);
         if (h->num_sms <= 0) h->num_sms = 1;
     }
+    // lbm_get_rho_u_static's array is placed now, while the device has room
+    h->static_stage = lbm_internal_static_stage();
     for (int c = 0; c < copies; ++c)
         if (h->cuda(cudaMemsetAsync(h->f[c], 0, fbytes, h->stream), "memset") != LBM_OK) {
             lbm_destroy(h);
@@ -707,6 +709,8 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
 }
 
 }  // namespace
+
+lbm_status lbm_internal_check_status(lbm_handle* h) { return check_status(h); }
 
 lbm_status lbm_internal_step(lbm_handle* h, cudaStream_t s) {
     return h->fp64() ? launch_one_step(h, h->kd, s) : launch_one_step(h, h->kf, s);

@@ -44,6 +44,7 @@ struct lbm_handle {
     lbm_status sticky = LBM_OK;
     std::string err;
     KernelSet* ks = nullptr;
+    double* static_stage = nullptr;   // device address of the readback array of lbm_get_rho_u_static
     Relax<float> kf{};
     Relax<double> kd{};
     size_t device_bytes = 0;
@@ -124,3 +125,10 @@ struct lbm_handle {
 
 // one stream-collide step of h launched on stream s (advances h's counters)
 lbm_status lbm_internal_step(lbm_handle* h, cudaStream_t s);
+// reads the device status word of h (after a stream synchronisation):
+// LBM_ERR_TIMEOUT, and the handle poisoned, if a bounded wait gave up
+lbm_status lbm_internal_check_status(lbm_handle* h);
+// device address of lbm_get_rho_u_static's staging array on the current
+// device, looked up once per device; NULL if the look-up failed (the CUDA
+// error is cleared)
+double* lbm_internal_static_stage();

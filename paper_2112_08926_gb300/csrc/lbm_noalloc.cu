@@ -7,10 +7,13 @@
 // processes where another framework owns the device memory pool, or where a
 // blocking cudaMalloc would stall other streams in the middle of a time loop,
 // allocating is not acceptable.  lbm_get_rho_u_static runs the same
-// field-probe kernel but stages through the fixed array below, which every
-// GPU that loads this library holds until the process exits.
+// field-probe kernel but stages through the fixed array below.  Its device
+// address is looked up when the first lattice on a device is created (which
+// also makes the runtime place the array there), so a readback in the middle
+// of a run takes no memory.
 #include <cuda_runtime.h>
 
+#include <mutex>
 #include <string>
 
 #include "lbm.h"
@@ -24,25 +27,9 @@ constexpr size_t kStaticDoubles = size_t(1) << 20;   // 8 MiB per device
 static __device__ __align__(256) double g_rho_u_stage[kStaticDoubles];
 
 constexpr int kMaxDevices = 64;
+std::mutex g_stage_mutex;
 double* g_stage_addr[kMaxDevices] = {};   // device address of g_rho_u_stage, per device
-
-// Device address of the staging array for the current device.  In host code
-// the array's name only stands for the symbol, so the address is asked for
-// once per device, with that device current.
-cudaError_t stage_address(double** out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_stage_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_rho_u_stage);
-        if (e != cudaSuccess) return e;
-        g_stage_addr[dev] = static_cast<double*>(p);
-    }
-    *out = g_stage_addr[dev];
-    return cudaSuccess;
-}
+bool g_stage_tried[kMaxDevices] = {};     // look-up done (g_stage_addr stays NULL if it failed)
 
 template <class R>
 lbm_status fields_static(lbm_handle* h, const Relax<R>& k, double* stage, double* dst[4]) {
@@ -74,6 +61,25 @@ lbm_status fields_static(lbm_handle* h, const Relax<R>& k, double* stage, double
 
 }  // namespace
 
+// In host code the array's name only stands for the symbol, so its device
+// address is asked for once per device, with that device current.
+double* lbm_internal_static_stage() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lock(g_stage_mutex);
+    if (!g_stage_tried[dev]) {
+        g_stage_tried[dev] = true;
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_rho_u_stage) == cudaSuccess) g_stage_addr[dev] = static_cast<double*>(p);
+        else cudaGetLastError();   // not sticky: the lattice itself is unaffected
+    }
+    return g_stage_addr[dev];
+}
+
 extern "C" lbm_status lbm_get_rho_u_static(lbm_handle* h, double* rho, double* ux, double* uy, double* uz) {
     if (!h) return LBM_ERR_ARG;
     if (h->sticky != LBM_OK) return LBM_ERR_STATE;
@@ -83,8 +89,12 @@ extern "C" lbm_status lbm_get_rho_u_static(lbm_handle* h, double* rho, double* u
                        "lbm_get_rho_u_static: an xy-plane needs " + std::to_string(4 * plane) +
                            " doubles of staging, the static buffer holds " + std::to_string(kStaticDoubles) +
                            " (nx*ny must not exceed 262144); use lbm_get_rho_u");
-    double* stage = nullptr;
-    if (h->cuda(stage_address(&stage), "cudaGetSymbolAddress")) return LBM_ERR_CUDA;
+    if (!h->static_stage)
+        return h->fail(LBM_ERR_UNSUPPORTED,
+                       "lbm_get_rho_u_static: the static staging array could not be placed on this device "
+                       "when the lattice was created; use lbm_get_rho_u");
     double* dst[4] = {rho, ux, uy, uz};
-    return h->fp64() ? fields_static(h, h->kd, stage, dst) : fields_static(h, h->kf, stage, dst);
+    const lbm_status st = h->fp64() ? fields_static(h, h->kd, h->static_stage, dst)
+                                    : fields_static(h, h->kf, h->static_stage, dst);
+    return st == LBM_OK ? lbm_internal_check_status(h) : st;
 }
