@@ -35,6 +35,13 @@
  *     single bit that does fit when 13 regime zeros are present;
  *   - NaN inputs: see fp16c_from_float; posit encoders saturate a NaN with
  *     the sign of the input.
+ *
+ * Pins (tests/test_oracle_codecs.py): the posit encoders equal the rounding
+ * of the exact posit bit string (Sec. 3.2.1 representation, half up on the
+ * first bit cut off) over the whole FP32 range, end rules included, except
+ * P16_2C below 2^-52: there the printed routine rounds the lowest numbers up
+ * with increments of its own, which this file follows as value rules; that
+ * sub-range is parity unpinned (its only check restates those rules).
  */
 #include "oracle.h"
 

@@ -3,8 +3,9 @@
 Each test checks the oracle (oracle/codecs.cpp) against something other than
 itself: bit patterns printed in Fig. 2, properties printed in Table 2, accuracy
 intervals stated in Sec. 3.2.2, numpy's IEEE binary16 conversion, the prose
-FP16C algorithm of Sec. 3.1.4, and brute-force nearest-value search over the
-decoded code table.
+FP16C algorithm of Sec. 3.1.4, brute-force nearest-value search over the
+decoded code table, and posit bit strings built from the representation of
+Sec. 3.2.1 (sign, regime run and terminator, exponent bits, mantissa).
 """
 import numpy as np
 import pytest
@@ -233,3 +234,141 @@ def test_fp16c_nan_rule():
                   0xFF800001, 0xFFFFF7FF, 0xFFFFF800, 0xFFFFFFFF], dtype=np.uint32)
     got = oracle.encode("FP16C", b.view(np.float32)).tolist()
     assert got == [0x7FFF, 0x7FFF, 0x8000, 0x8000, 0xFFFF, 0xFFFF, 0x0000, 0x0000]
+
+
+# ---------------------------------------------------------------- posit bit strings
+# (exponent bits es, scale 2^k applied before encoding, asymmetric lower-flank regime)
+POSITS = {"P16_0": (0, 0, False), "P16_0S": (0, 7, False), "P16_1": (1, 0, False),
+          "P16_1S": (1, 7, False), "P16_2C": (2, 0, True)}
+
+
+def _posit_bitstring_encode(x, es, scale, asym):
+    """FP32 -> 16-bit posit code by rounding the exact bit string, written
+    from the representation of Sec. 3.2.1: x 2^scale = 2^(r 2^es + e)(1 + m),
+    regime r as a run of ones ending in a zero (r >= 0: r+1 ones) or zeros
+    ending in a one (r < 0: -r zeros), then es exponent bits, then the 23
+    FP32 mantissa bits.  The 15 magnitude bits are the first 15 of that
+    string and the first bit cut off is added (half up).  The asymmetric
+    P16_2C covers [0, 2) only: v zeros, a one, two exponent bits holding
+    3 - ((-E) mod 4) for v = floor(-E / 4); a carry out of its 15 bits is lost.
+    Zeros, FP32 subnormals and values whose regime fills all 16 bits give
+    code 0; values from the largest code on, Inf and NaN give the largest
+    code; the sign bit is copied."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.int64)
+    sign = (b >> 16) & 0x8000
+    ef = (b >> 23) & 0xFF
+    m = b & 0x7FFFFF
+    E = ef - 127 + scale
+    if asym:
+        sat = E >= 1
+        ae = np.maximum(-E, 0)
+        zeros = ae >> 2
+        e = 3 - (ae & 3)
+        lead = np.ones_like(E)
+        rl = zeros + 1
+    else:
+        sat = E >= 14 * (1 << es)          # the largest code, 2^(14 2^es)
+        K = E >> es                        # floor(E / 2^es)
+        e = E - (K << es)
+        neg = K < 0
+        zeros = np.where(neg, -K, 0)
+        ones = np.clip(np.where(neg, 0, K + 1), 0, 40)
+        lead = np.where(neg, 1, ((np.int64(1) << ones) - 1) << 1)
+        rl = np.where(neg, zeros + 1, ones + 1)
+    under = zeros >= 16
+    L = np.where(under, 1, rl) + es + 23   # length of the bit string
+    bits = (lead << (es + 23)) | (e << 23) | m
+    mag = (bits >> (L - 15)) + ((bits >> (L - 16)) & 1)
+    if asym:
+        mag = mag & 0x7FFF
+    mag = np.where(under | (ef == 0), 0, mag)
+    mag = np.where(sat | (ef == 255), 0x7FFF, mag)
+    return (sign | mag).astype(np.uint16)
+
+
+def _posit_decode_from_representation(codes, es, scale, asym):
+    """Value of each code from Sec. 3.2.1's representation (exact in float64):
+    regime from the run length, then the exponent bits that fit (missing low
+    exponent bits read as zero), then the mantissa bits that are left."""
+    out = np.empty(codes.size, dtype=np.float64)
+    for k, c in enumerate(codes.tolist()):
+        mag, s = c & 0x7FFF, -1.0 if c & 0x8000 else 1.0
+        if mag == 0:
+            out[k] = s * 0.0
+            continue
+        bits = format(mag, "015b")
+        if asym:
+            n = len(bits) - len(bits.lstrip("0"))
+            r, rest = -n, bits[n + 1:]
+        else:
+            n = len(bits) - len(bits.lstrip(bits[0]))
+            r = n - 1 if bits[0] == "1" else -n
+            rest = bits[n + 1:]
+        ebits = rest[:es]
+        e = int(ebits, 2) << (es - len(ebits)) if ebits else 0
+        frac = rest[es:]
+        f = int(frac, 2) / 2.0 ** len(frac) if frac else 0.0
+        if asym:
+            E = -3 + 4 * r + e            # v = -r zeros: 2^(-4v + e - 3)
+        else:
+            E = r * (1 << es) + e - scale
+        out[k] = s * 2.0 ** E * (1.0 + f)
+    return out
+
+
+def _dense_floats(seed):
+    """Every FP32 exponent with 4096 mantissas (a regular grid, random ones
+    and the binade edges), 4M random bit patterns, both signs."""
+    rng = np.random.default_rng(seed)
+    exps = np.arange(256, dtype=np.uint32) << 23
+    mants = np.concatenate([np.arange(0, 1 << 23, 4096, dtype=np.uint32),
+                            rng.integers(0, 1 << 23, 2043, dtype=np.uint64).astype(np.uint32),
+                            np.array([1, 0x7FFFFF, 0x400000, 0x3FFFFF, 0x400001], dtype=np.uint32)])
+    bits = (exps[:, None] | mants[None, :]).ravel()
+    bits = np.concatenate([bits, rng.integers(0, 1 << 32, 1 << 22, dtype=np.uint64).astype(np.uint32)])
+    return np.concatenate([bits, bits ^ np.uint32(0x80000000)]).view(np.float32)
+
+
+@pytest.mark.parametrize("fmt", sorted(POSITS))
+def test_posit_encode_rounds_the_representation_bit_string(fmt):
+    """The oracle's posit encoders are written as nearest-value rules with
+    end rules read off the printed conversions; here they must equal a
+    different construction, rounding of the exact bit string, over the whole
+    FP32 range (every exponent, NaN and Inf included).  That covers the end
+    rules of P16_0 and P16_1 (where the exponent bit no longer fits) and
+    P16_2C's carry out of range just below 2.  The one exception is P16_2C
+    below 2^-52, where the printed routine rounds the lowest numbers up with
+    its own increments instead (the oracle follows it there; that range is
+    pinned only by test_posit_end_rules)."""
+    es, scale, asym = POSITS[fmt]
+    x = _dense_floats(20211216)
+    got = oracle.encode(fmt, x)
+    ref = _posit_bitstring_encode(x, es, scale, asym)
+    bad = got != ref
+    if fmt == "P16_2C":
+        ax = np.abs(x[bad].astype(np.float64))
+        assert np.all(ax < 2.0 ** -52)
+        assert bad.sum() > 0
+        assert np.array_equal(got[~bad], ref[~bad])
+    else:
+        assert not bad.any(), [hex(v) for v in x[bad][:5].view(np.uint32)]
+
+
+@pytest.mark.parametrize("fmt", sorted(POSITS))
+def test_posit_decode_is_the_representation_value(fmt):
+    """All 65536 codes against Sec. 3.2.1's representation.  The only
+    difference: P16_2C codes with 13 regime zeros, where one exponent bit
+    still fits; the printed decoder reads it as zero, so code 3 decodes to
+    2^-55 instead of 2^-53 (the same reading as the oracle's)."""
+    es, scale, asym = POSITS[fmt]
+    codes = np.arange(0x10000, dtype=np.uint16)
+    got = oracle.decode(fmt, codes).astype(np.float64)
+    ref = _posit_decode_from_representation(codes, es, scale, asym)
+    bad = np.flatnonzero(got != ref)
+    if fmt == "P16_2C":
+        assert [int(c) for c in codes[bad]] == [0x0003, 0x8003]
+        assert np.array_equal(got[bad], np.array([2.0 ** -55, -2.0 ** -55]))
+        assert np.array_equal(ref[bad], np.array([2.0 ** -53, -2.0 ** -53]))
+    else:
+        assert bad.size == 0
+    assert np.array_equal(np.signbit(got), np.signbit(ref))
