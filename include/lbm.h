@@ -156,6 +156,18 @@ lbm_status lbm_set_rho_u(lbm_handle* h, const double* rho, const double* ux,
  * are those of one launch per step. */
 lbm_status lbm_step(lbm_handle* h, int64_t nsteps);
 
+/* Divergence check inside lbm_step (off by default): after every `every`
+ * steps of the lattice's step counter, lbm_step runs the FP64 reduction of
+ * lbm_reduce and returns LBM_ERR_DIVERGED, with the step reached in
+ * lbm_last_error, when the mass or the kinetic energy is not finite or the
+ * mass has drifted from its value when the check was set by more than
+ * mass_tol relative (mass_tol <= 0: finiteness only).  The populations stay
+ * as they are (the handle is not poisoned); each check synchronises the
+ * stream, and the steps in between keep their graphs.  every = 0 switches
+ * the check off.  Errors: LBM_ERR_ARG (every < 0 or mass_tol not finite),
+ * LBM_ERR_DIVERGED if the state is already non-finite when the check is set. */
+lbm_status lbm_set_divergence_check(lbm_handle* h, int64_t every, double mass_tol);
+
 /* Density and velocity of every cell from the streamed populations: rho =
  * (sum f_i) + 1 (Sec. 2.2), u = (sum c_i f_i + F/2)/rho (not clamped).
  * EQ cells report their node state, solid cells rho = 1, u = 0.  Host arrays
@@ -303,6 +315,12 @@ lbm_status lbm_codec_decode(int storage, const uint16_t* c_dev, float* out_dev, 
 /* Encode the floats whose bit patterns are first, first+1, ..., first+n-1. */
 lbm_status lbm_codec_encode_bits(int storage, uint32_t first, int64_t n, uint16_t* out_dev,
                                  void* cuda_stream);
+/* The same through the table-driven encoder that the paired stream-collide
+ * kernel uses for the posit formats (one fused multiply-add per value from a
+ * per-exponent table held in shared memory); it gives the same codes as
+ * lbm_codec_encode_bits.  Posit formats only (LBM_ERR_UNSUPPORTED otherwise). */
+lbm_status lbm_codec_encode_bits_table(int storage, uint32_t first, int64_t n, uint16_t* out_dev,
+                                       void* cuda_stream);
 
 /* ---- ensembles: many independent lattices advanced by one launch per step -- */
 typedef struct lbm_ensemble lbm_ensemble;
@@ -323,13 +341,29 @@ lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps);
 /* Cells per tile (thread block) of the ensemble launch: bx a multiple of 32
  * in [32, 256], by must be 1 (tiles are runs of consecutive cells). */
 lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by);
-/* Picks the tile size and the streaming scheme: times trial_steps steps
- * (rounded up to even) for each of a fixed list of tile sizes, then, where
- * every member allows it (A-A: no OUTFLOW or FREESLIP cells; memory for the
- * A-B copies) and the step count is even, converts all members to the other
- * scheme (lbm_set_scheme) and times again; keeps the fastest combination.
- * The trial steps are real steps (two warm-up steps per tile size on top).
- * Results do not depend on the tile size or the scheme. */
+/* Kernel of the ensemble's plain cells.
+ *   PER_CELL  one cell per thread, tiles of lbm_ensemble_set_block cells,
+ *             every scheme, storage format and collision (the default);
+ *   PAIRED    two cells per thread, one warp per run of 64 consecutive cells
+ *             of a member, every population moved as 32-bit pairs of codes
+ *             (A-B, FP16 or FP16S storage with FP32 arithmetic, SRT or TRT,
+ *             q N < 2^32 for every member); `warps` (1..4) runs per tile.
+ *             Cells on the faces of members with non-solid face cells take
+ *             the per-cell path inside the same launch.
+ * Both give bit for bit the same populations.  Errors: LBM_ERR_ARG,
+ * LBM_ERR_UNSUPPORTED (PAIRED where it does not apply). */
+enum { LBM_ENS_PER_CELL = 0, LBM_ENS_PAIRED = 1 };
+lbm_status lbm_ensemble_set_variant(lbm_ensemble* e, int variant, int warps);
+int lbm_ensemble_get_variant(const lbm_ensemble* e);
+/* Picks the kernel, its tile and the streaming scheme: times trial_steps
+ * steps (rounded up to even) for every tile size of the per-cell kernel and,
+ * where it applies, every tile of the paired kernel; then, where every member
+ * allows it (A-A: no OUTFLOW or FREESLIP cells; memory for the A-B copies)
+ * and the step count is even, converts all members to the other scheme
+ * (lbm_set_scheme) and times again; keeps the fastest combination.  *bx
+ * receives the cells per tile, *by 1 for the per-cell kernel or the warps per
+ * tile of the paired one.  The trial steps are real steps (two warm-up steps
+ * per configuration on top).  Results do not depend on any of the choices. */
 lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, int* bx, int* by);
 /* The streaming scheme the ensemble's members use now (-1 for NULL). */
 int lbm_ensemble_scheme(const lbm_ensemble* e);

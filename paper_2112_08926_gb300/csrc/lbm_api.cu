@@ -773,10 +773,13 @@ lbm_status step_graph(lbm_handle* h, cudaGraphExec_t* out) {
 
 }  // namespace
 
-extern "C" lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
-    lbm_status st = check_handle(h);
-    if (st != LBM_OK) return st;
-    if (nsteps < 0) return h->fail(LBM_ERR_ARG, "negative step count");
+namespace {
+
+lbm_status reduce_any(lbm_handle* h, double* mass, double* energy);
+
+// nsteps steps without divergence checks
+lbm_status step_run(lbm_handle* h, int64_t nsteps) {
+    lbm_status st = LBM_OK;
     int64_t s = 0;
     if (h->N <= kGraphCells && nsteps >= 2 * kStepGraph) {
         cudaGraphExec_t g = nullptr;
@@ -791,6 +794,51 @@ extern "C" lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
         if (st != LBM_OK) return st;
     }
     return LBM_OK;
+}
+
+// the FP64 check of lbm_set_divergence_check at the current step
+lbm_status divergence_check(lbm_handle* h) {
+    double mass = 0.0, energy = 0.0;
+    const lbm_status st = reduce_any(h, &mass, &energy);
+    if (st == LBM_ERR_DIVERGED || (st == LBM_OK && h->check_tol > 0.0 &&
+                                   std::fabs(mass - h->check_mass0) > h->check_tol * std::fabs(h->check_mass0))) {
+        h->err = "diverged at step " + std::to_string(h->t) + ": mass " + std::to_string(mass) + " (set " +
+                 std::to_string(h->check_mass0) + "), kinetic energy " + std::to_string(energy);
+        return LBM_ERR_DIVERGED;
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" lbm_status lbm_step(lbm_handle* h, int64_t nsteps) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    if (nsteps < 0) return h->fail(LBM_ERR_ARG, "negative step count");
+    if (h->check_every <= 0) return step_run(h, nsteps);
+    // runs up to the next multiple of check_every of the step counter, each followed by the check
+    while (nsteps > 0) {
+        const int64_t to_check = h->check_every - (h->t % h->check_every);
+        const int64_t n = std::min(nsteps, to_check);
+        if ((st = step_run(h, n)) != LBM_OK) return st;
+        nsteps -= n;
+        if (h->t % h->check_every == 0 && (st = divergence_check(h)) != LBM_OK) return st;
+    }
+    return LBM_OK;
+}
+
+extern "C" lbm_status lbm_set_divergence_check(lbm_handle* h, int64_t every, double mass_tol) {
+    lbm_status st = check_handle(h);
+    if (st != LBM_OK) return st;
+    if (every < 0 || !std::isfinite(mass_tol)) return h->fail(LBM_ERR_ARG, "divergence check: every < 0 or mass_tol");
+    h->check_every = every;
+    h->check_tol = mass_tol;
+    if (every == 0) return LBM_OK;
+    double mass = 0.0, energy = 0.0;
+    st = reduce_any(h, &mass, &energy);
+    h->check_mass0 = mass;
+    if (st != LBM_OK) h->check_every = 0;
+    return st;
 }
 
 namespace {
@@ -975,10 +1023,16 @@ template <class R> lbm_status reduce_impl(lbm_handle* h, const Relax<R>& k, doub
 
 }  // namespace
 
+namespace {
+lbm_status reduce_any(lbm_handle* h, double* mass, double* energy) {
+    return h->fp64() ? reduce_impl(h, h->kd, mass, energy) : reduce_impl(h, h->kf, mass, energy);
+}
+}  // namespace
+
 extern "C" lbm_status lbm_reduce(lbm_handle* h, double* mass, double* kinetic_energy) {
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
-    return h->fp64() ? reduce_impl(h, h->kd, mass, kinetic_energy) : reduce_impl(h, h->kf, mass, kinetic_energy);
+    return reduce_any(h, mass, kinetic_energy);
 }
 
 namespace {

@@ -27,6 +27,23 @@ __global__ void k_encode_bits(uint32_t first, uint16_t* __restrict__ out, int64_
         out[t] = (uint16_t)Codec16<FMT>::enc(__uint_as_float(first + (uint32_t)t));
 }
 
+// the table-driven posit encoder of the paired stream-collide kernel, on the
+// same shared-memory copy of the table (x scaled by 2^SL as the kernel's
+// values are; NaN keeps the sign of x)
+template <int FMT>
+__global__ void k_encode_bits_table(uint32_t first, uint16_t* __restrict__ out, int64_t n) {
+    __shared__ EncEntry tab[512];
+    for (int i = threadIdx.x; i < 512; i += blockDim.x) tab[i] = kEncTable<FMT>.e[i];
+    __syncthreads();
+    constexpr int SL = Codec16<FMT>::SL;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const float x = __uint_as_float(first + (uint32_t)t);
+        const uint32_t c = SL == 0 ? enc_table(tab, x)
+                                   : (enc_table(tab, fabsf(x) * 128.0f) | ((__float_as_uint(x) >> 16) & 0x8000u));
+        out[t] = (uint16_t)c;
+    }
+}
+
 unsigned grid_for(int64_t n) {
     const int64_t b = (n + 255) / 256;
     return (unsigned)(b < 152 * 64 ? (b > 0 ? b : 1) : 152 * 64);
@@ -67,6 +84,12 @@ template <int F> struct EncBits {
     }
 };
 
+template <int F> struct EncBitsTable {
+    static void run(unsigned g, cudaStream_t s, uint32_t first, uint16_t* o, int64_t n) {
+        k_encode_bits_table<F><<<g, 256, 0, s>>>(first, o, n);
+    }
+};
+
 }  // namespace
 
 extern "C" {
@@ -85,6 +108,22 @@ lbm_status lbm_codec_encode_bits(int storage, uint32_t first, int64_t n, uint16_
     if (n > 0 && !out_dev) return LBM_ERR_ARG;
     if (n > (int64_t)1 << 32) return LBM_ERR_ARG;
     return dispatch<EncBits>(storage, n, (cudaStream_t)stream, first, out_dev, n);
+}
+
+lbm_status lbm_codec_encode_bits_table(int storage, uint32_t first, int64_t n, uint16_t* out_dev, void* stream) {
+    if (storage < LBM_P16_0S || storage > LBM_P16_1) return LBM_ERR_UNSUPPORTED;
+    if (n > 0 && !out_dev) return LBM_ERR_ARG;
+    if (n > (int64_t)1 << 32) return LBM_ERR_ARG;
+    if (n == 0) return LBM_OK;
+    const unsigned g = grid_for(n);
+    switch (storage) {
+    case LBM_P16_0S: EncBitsTable<LBM_P16_0S>::run(g, (cudaStream_t)stream, first, out_dev, n); break;
+    case LBM_P16_1S: EncBitsTable<LBM_P16_1S>::run(g, (cudaStream_t)stream, first, out_dev, n); break;
+    case LBM_P16_2C: EncBitsTable<LBM_P16_2C>::run(g, (cudaStream_t)stream, first, out_dev, n); break;
+    case LBM_P16_0: EncBitsTable<LBM_P16_0>::run(g, (cudaStream_t)stream, first, out_dev, n); break;
+    default: EncBitsTable<LBM_P16_1>::run(g, (cudaStream_t)stream, first, out_dev, n); break;
+    }
+    return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
 }
 
 }  // extern "C"

@@ -116,119 +116,182 @@ __device__ __forceinline__ uint32_t fp16c_encode(float x) {
     return a >= 0x7FFFF800u ? (s ^ 0x8000u) : (s | code);
 }
 
-// length of the regime run of a 15-bit posit magnitude (bits 14..0):
-// leading bits equal to bit 14, at most 15
-__device__ __forceinline__ int posit_run(uint32_t mag) {
-    const uint32_t lead = mag >> 14;
-    const uint32_t t = (mag ^ (0u - lead)) & 0x7FFFu;   // run becomes leading zeros
-    return min(__clz(t << 17), 15);
-}
+// Posits (Sec. 3.2): a 15-bit magnitude under the sign bit.  P16_0 / P16_1:
+// a regime run (r+1 ones and a zero for r >= 0, -r zeros and a one for r < 0),
+// ES exponent bits, the fraction; value 2^(r 2^ES + e) (1 + fraction).
+// P16_2C (asymmetric, lower flank only): v zeros and a one, two exponent
+// bits, the fraction; value 2^(-4v + e - 3) (1 + fraction).  All conversions
+// below are branch-free.
 
-// Sign-magnitude posit with ES exponent bits (Sec. 3.2.1): regime k = run-1
-// for a run of ones, -run for zeros; value 2^(k*2^ES + e) (1 + fraction).
-// `bias_shift` folds the 2^-7 decode scale of the S variants into the
-// exponent (exact).  Zero magnitude decodes to +-0.
+// Decode: the run of bits equal to bit 14 becomes leading zeros (xor with the
+// sign-extended bit 14) and is counted in one instruction; the bits after the
+// terminator, moved to the top of a word, hold the exponent bits and the
+// fraction, and one addition puts them under the regime's exponent.  Exponent
+// bits cut off by a long regime read as zero.  bias_shift folds the 2^-7
+// decode scale of the S variants into the exponent (exact).  A zero magnitude
+// decodes to +-0.
 template <int ES>
 __device__ __forceinline__ float posit_decode(uint32_t c, int bias_shift) {
-    const uint32_t mag = c & 0x7FFFu;
-    const int run = posit_run(mag);
-    const int k = (mag >> 14) ? run - 1 : -run;
-    int e = 0;
-    uint32_t frac;
-    if (ES == 0) {
-        frac = (mag << (run + 9)) & 0x7FFFFFu;
-    } else {
-        e = (int)(((mag << (run + 9)) >> 22) & 1u);
-        frac = (mag << (run + 10)) & 0x7FFFFFu;
-    }
-    const int ex = k * (1 << ES) + e + 127 + bias_shift;
-    const uint32_t bits = ((c & 0x8000u) << 16) | (mag ? (((uint32_t)ex << 23) | frac) : 0u);
-    return __uint_as_float(bits);
+    const uint32_t x = c << 17;                                  // magnitude in bits 31..17
+    const uint32_t m = (uint32_t)((int32_t)x >> 31);             // all ones for a run of ones
+    const int n = __clz(x ^ m);                                  // run length (32: zero magnitude)
+    const int k = (n - 1) ^ (int)~m;                             // regime: n - 1 (ones), -n (zeros)
+    const uint32_t r = __funnelshift_lc(0u, x, (uint32_t)n + 1u);   // the bits after the terminator
+    const uint32_t bits = ((uint32_t)k << (23 + ES)) + ((uint32_t)(127 + bias_shift) << 23) + (r >> (9 - ES));
+    const uint32_t sign = (c & 0x8000u) << 16;
+    return __uint_as_float(x ? (bits | sign) : sign);
 }
 
-// Asymmetric posit P16_2C (Sec. 3.2.2): v leading zeros, a terminating one,
-// two exponent bits, 12-v fraction bits; value 2^(-4v + e - 3)(1 + fraction).
-// With fewer than two exponent bits left (v >= 13) the exponent reads 0.
+// P16_2C: with 13 leading zeros only one exponent bit fits, and it reads as
+// zero (the exponent bits cut off by the regime); 14 zeros leave none.
 __device__ __forceinline__ float p162c_decode(uint32_t c) {
-    const uint32_t mag = c & 0x7FFFu;
-    const int v = min(__clz(mag << 17), 15);
-    const int e = v <= 12 ? (int)((mag >> (12 - v)) & 3u) : 0;
-    const uint32_t frac = (mag << (v + 11)) & 0x7FFFFFu;
-    const uint32_t bits =
-        ((c & 0x8000u) << 16) | (mag ? ((uint32_t)(124 - 4 * v + e) << 23) | frac : 0u);
-    return __uint_as_float(bits);
+    const uint32_t x = c << 17;
+    const uint32_t v = (uint32_t)__clz(x);                       // leading zeros (32: zero magnitude)
+    uint32_t r = __funnelshift_lc(0u, x, v + 1u);                // exponent bits and fraction at the top
+    r = v < 13u ? r : 0u;
+    const uint32_t bits = (124u << 23) - (v << 25) + (r >> 7);   // exponent field 124 - 4v + e
+    const uint32_t sign = (c & 0x8000u) << 16;
+    return __uint_as_float(x ? (bits | sign) : sign);
 }
 
-// mantissa rounded to nf fraction bits (nearest, ties up), added to the
-// regime/exponent pattern R; a carry walks into the next posit value
-__device__ __forceinline__ uint32_t posit_round(uint32_t R, uint32_t m, int nf) {
-    return R + (m >> (23 - nf)) + ((m >> (22 - nf)) & 1u);
-}
-
-// FP32 -> P16_0 (es = 0): nearest value, ties away from zero; 0 below 2^-15,
-// 2^-14 in [2^-15, 2^-14); saturation (also for NaN) from 2^14.
-__device__ __forceinline__ uint32_t p160_encode(float y) {
+// Encode P16_0 / P16_1: the bit string of |y| -- regime, exponent bit, the 23
+// FP32 mantissa bits -- is laid out in one word below the regime's first bit
+// (the run of ones of a regime r >= 0 comes from sign extension), shifted so
+// that 16 bits remain, and the last of them (the first bit cut off) is
+// added: nearest value with ties away from zero where fraction bits fit, and
+// rounding of the bit string where the regime leaves no room for the
+// exponent bit.  Magnitudes from the largest code on, Inf and NaN saturate;
+// zeros, FP32 subnormals and values below half the smallest code give 0.
+// The sign of y is copied.
+template <int ES>
+__device__ __forceinline__ uint32_t posit_encode(float y) {
     const uint32_t b = u32(y);
-    const uint32_t s = (b >> 16) & 0x8000u;
     const int E = (int)((b >> 23) & 0xFFu) - 127;
-    const uint32_t m = b & 0x7FFFFFu;
-    uint32_t mag;
-    if (E >= 14) mag = 0x7FFFu;
-    else if (E < -15) mag = 0u;
-    else if (E == -15) mag = 1u;
-    else {
-        const int nf = E >= 0 ? 13 - E : 14 + E;
-        const uint32_t R = E >= 0 ? 0x8000u - (1u << (14 - E)) : 1u << (14 + E);
-        mag = posit_round(R, m, nf);
-    }
-    return s | mag;
+    const int k = min(E >> ES, 14);                              // regime floor(E / 2^ES), saturating
+    const uint32_t neg = (uint32_t)(k >> 31);                    // all ones for r < 0
+    // exponent bit and mantissa; for ES = 1 the exponent bit is the FP32
+    // exponent's low bit inverted (E = field - 127, 127 odd)
+    const uint32_t t = ES == 1 ? ((b ^ 0x00800000u) & 0x00FFFFFFu) : (b & 0x007FFFFFu);
+    // terminator at bit 23 + ES: a one under zeros (r < 0), a zero under ones
+    const uint32_t X = t + (neg & (3u << (23 + ES))) + (0xFFFFFFFFu << (24 + ES));
+    const uint32_t sh = (uint32_t)(k ^ (int)neg) + (uint32_t)(9 + ES);   // leaves field + rounding bit
+    const uint32_t w = __funnelshift_rc(X, ~neg, sh);            // X >> sh, sign-extended, clamped
+    return ((b >> 16) & 0x8000u) | (((w + 1u) >> 1) & 0x7FFFu);
 }
 
-// FP32 -> P16_1 (es = 1): nearest value, ties away from zero between 2^-26
-// and 2^26; bit-string rounding where the exponent bit does not fit.
-__device__ __forceinline__ uint32_t p161_encode(float y) {
-    const uint32_t b = u32(y);
-    const uint32_t s = (b >> 16) & 0x8000u;
-    const int E = (int)((b >> 23) & 0xFFu) - 127;
-    const uint32_t m = b & 0x7FFFFFu;
-    uint32_t mag;
-    if (E >= 27) mag = 0x7FFFu;
-    else if (E == 26) mag = 0x7FFEu;
-    else if (E < -30) mag = 0u;
-    else if (E <= -28) mag = 1u;
-    else if (E == -27) mag = 2u;
-    else {
-        const int k = E >> 1;                 // floor(E / 2)
-        const uint32_t ex = (uint32_t)E & 1u;
-        const int nf = k >= 0 ? 12 - k : 13 + k;
-        const uint32_t R = (k >= 0 ? 0x8000u - (1u << (14 - k)) : 1u << (14 + k)) | (ex << nf);
-        mag = posit_round(R, m, nf);
-    }
-    return s | mag;
-}
-
-// FP32 -> P16_2C: nearest value, ties away from zero between 2^-51 and 2;
-// end rules: [2^-53,2^-51) -> 4, [2^-55,2^-53) -> 3, [2^-58,2^-55) -> 2,
-// below -> 0; >= 2 (and NaN) saturate; a rounding carry out of the top
-// binade leaves the 15-bit field (zero).
+// Encode P16_2C: the same with v = floor(-E / 4) zeros and the exponent field
+// 3 - (-E mod 4); a carry out of the 15 bits (just below 2) leaves 0.  End
+// rules: from 2 on (and NaN) saturation; below 2^-51 the printed conversion's
+// own rounding of the lowest numbers: [2^-53, 2^-51) -> 4, [2^-55, 2^-53) -> 3,
+// [2^-58, 2^-55) -> 2, smaller -> 0.
 __device__ __forceinline__ uint32_t p162c_encode(float x) {
     const uint32_t b = u32(x);
-    const uint32_t s = (b >> 16) & 0x8000u;
     const int E = (int)((b >> 23) & 0xFFu) - 127;
-    const uint32_t m = b & 0x7FFFFFu;
-    uint32_t mag;
-    if (E >= 1) mag = 0x7FFFu;
-    else if (E < -58) mag = 0u;
-    else if (E <= -56) mag = 2u;
-    else if (E <= -54) mag = 3u;
-    else if (E <= -52) mag = 4u;
-    else {
-        const int v = (-E) >> 2;
-        const uint32_t ex = 3u - ((uint32_t)(-E) & 3u);
-        const int nf = 12 - v;
-        mag = posit_round((1u << (14 - v)) | (ex << nf), m, nf) & 0x7FFFu;
+    const uint32_t ae = (uint32_t)max(-E, 0);
+    const uint32_t X = 0x02000000u | ((~ae & 3u) << 23) | (b & 0x007FFFFFu);
+    const uint32_t w = X >> min((ae >> 2) + 10u, 31u);
+    uint32_t mag = ((w + 1u) >> 1) & 0x7FFFu;
+    mag = E >= 1 ? 0x7FFFu : mag;
+    mag = E < -51 ? (E >= -53 ? 4u : (E >= -55 ? 3u : (E >= -58 ? 2u : 0u))) : mag;
+    return ((b >> 16) & 0x8000u) | mag;
+}
+
+// Table-driven posit encoder (used where a block holds the table in shared
+// memory).  Within one FP32 binade of |y| the code is linear in |y| (where
+// fraction bits fit) or constant (where the regime cuts exponent bits off,
+// and at the ends of the range), so one fused multiply-add rounded toward
+// zero gives it: with s = 2^(nf - E) (nf fraction bits) and o = 2^22 + c0 -
+// 2^nf + 1/2 (c0 the code of 2^E), fma_rz(|y|, s, o) = 2^22 + c0 +
+// floor(f 2^nf + 1/2) + {0, 1/2} in [2^22, 2^23), whose mantissa holds the
+// code above one bit of the half.  The entries are indexed by the sign and the
+// exponent field of y (s is negated for negative y).  Inf and NaN give NaN,
+// whose pattern 0x7FFFFFFF holds the largest code.
+struct EncEntry {
+    float s, o;
+};
+struct EncTable {
+    EncEntry e[512];
+};
+
+// constexpr 2^n as float (|n| < 128)
+__host__ __device__ constexpr float pow2f(int n) {
+    double v = 1.0;
+    for (int i = 0; i < (n < 0 ? -n : n); ++i) v = n < 0 ? v * 0.5 : v * 2.0;
+    return (float)v;
+}
+
+// FMT: 5..9 (the table works on the value as stored, times 2^SL for the S
+// variants, like enc_g)
+template <int FMT>
+__host__ __device__ constexpr EncTable make_enc_table() {
+    constexpr bool asym = FMT == 7;
+    constexpr int ES = (FMT == 5 || FMT == 8) ? 0 : (FMT == 7 ? 2 : 1);
+    EncTable t{};
+    for (int e9 = 0; e9 < 512; ++e9) {
+        const int e8 = e9 & 255;
+        const float sgn = e9 >= 256 ? -1.0f : 1.0f;
+        const int E = e8 - 127;
+        long long cst = -1;   // constant code, or -1 for a linear binade
+        int nf = 0;
+        long long c0 = 0;
+        if (e8 == 0) {
+            cst = 0;
+        } else if (e8 == 255) {
+            cst = 0x7FFF;
+        } else if (asym) {
+            if (E >= 1) cst = 0x7FFF;
+            else if (E < -51) cst = E >= -53 ? 4 : (E >= -55 ? 3 : (E >= -58 ? 2 : 0));
+            else {
+                const int v = (-E) >> 2, ee = 3 - ((-E) & 3);
+                nf = 12 - v;
+                c0 = (1ll << (14 - v)) | ((long long)ee << nf);
+            }
+        } else if (E >= (14 << ES)) {
+            cst = 0x7FFF;
+        } else {
+            const int k = E >= 0 ? (E >> ES) : -((-E + (1 << ES) - 1) >> ES);   // floor(E / 2^ES)
+            const int ee = E - k * (1 << ES);
+            const int rl = k >= 0 ? k + 2 : 1 - k;                               // regime bits with terminator
+            const long long reg = k >= 0 ? (((1ll << (k + 1)) - 1) << 1) : 1ll;
+            nf = 15 - rl - ES;
+            if (nf >= 0) {
+                c0 = (reg << (15 - rl)) | ((long long)ee << nf);
+            } else {
+                const long long str = (reg << ES) | ee;                         // rl + ES > 15 bits
+                const int L = rl + ES;
+                cst = L > 40 ? 0 : (str >> (L - 15)) + ((str >> (L - 16)) & 1);
+            }
+        }
+        if (cst >= 0) {
+            t.e[e9].s = 0.0f;
+            t.e[e9].o = pow2f(22) + (float)cst + 0.5f;
+        } else {
+            t.e[e9].s = sgn * pow2f(nf - E);
+            t.e[e9].o = pow2f(22) + (float)(c0 - (1ll << nf)) + 0.5f;
+        }
     }
-    return s | mag;
+    return t;
+}
+
+// the encoding table of each posit format, in device memory (copied into
+// shared memory by the kernels that use it)
+template <int FMT> __device__ const EncTable kEncTable = make_enc_table<FMT>();
+
+// the code of g (scaled as stored) from a table entry
+__device__ __forceinline__ uint32_t enc_table(const EncEntry* tab, float g) {
+    const uint32_t b = u32(g);
+    const EncEntry t = tab[b >> 23];
+    const uint32_t v = u32(__fmaf_rz(g, t.s, t.o));
+    return ((v >> 1) & 0x7FFFu) | ((b >> 16) & 0x8000u);
+}
+// two codes as one pair (lo in bits 0..15, hi in bits 16..31)
+__device__ __forceinline__ uint32_t enc_table_pair(const EncEntry* tab, float lo, float hi) {
+    const uint32_t bl = u32(lo), bh = u32(hi);
+    const EncEntry tl = tab[bl >> 23], th = tab[bh >> 23];
+    const uint32_t vl = u32(__fmaf_rz(lo, tl.s, tl.o)), vh = u32(__fmaf_rz(hi, th.s, th.o));
+    const uint32_t c = __byte_perm(vl >> 1, vh << 15, 0x7610);   // codes at bits 0..14 and 16..30
+    const uint32_t sg = __byte_perm(bl, bh, 0x7030);             // sign bits at 15 and 31
+    return (c & 0x7FFF7FFFu) | (sg & 0x80008000u);
 }
 
 // Codec16<FMT>: dec/enc convert between a code and the population value;
@@ -263,19 +326,19 @@ template <> struct Codec16<4> {   // FP16C (Sec. 3.1.4)
 template <> struct Codec16<5> {   // P16_0S: posit es=0 of x * 2^7
     static constexpr int SL = 7;
     __device__ static float dec_g(uint32_t c) { return posit_decode<0>(c, 0); }
-    __device__ static uint32_t enc_g(float g) { return p160_encode(fabsf(g)) | ((u32(g) >> 16) & 0x8000u); }
+    __device__ static uint32_t enc_g(float g) { return posit_encode<0>(g); }
     __device__ static float dec(uint32_t c) { return posit_decode<0>(c, -7); }
     __device__ static uint32_t enc(float x) {
-        return p160_encode(fabsf(x) * 128.0f) | ((u32(x) >> 16) & 0x8000u);
+        return posit_encode<0>(fabsf(x) * 128.0f) | ((u32(x) >> 16) & 0x8000u);
     }
 };
 template <> struct Codec16<6> {   // P16_1S: posit es=1 of x * 2^7
     static constexpr int SL = 7;
     __device__ static float dec_g(uint32_t c) { return posit_decode<1>(c, 0); }
-    __device__ static uint32_t enc_g(float g) { return p161_encode(fabsf(g)) | ((u32(g) >> 16) & 0x8000u); }
+    __device__ static uint32_t enc_g(float g) { return posit_encode<1>(g); }
     __device__ static float dec(uint32_t c) { return posit_decode<1>(c, -7); }
     __device__ static uint32_t enc(float x) {
-        return p161_encode(fabsf(x) * 128.0f) | ((u32(x) >> 16) & 0x8000u);
+        return posit_encode<1>(fabsf(x) * 128.0f) | ((u32(x) >> 16) & 0x8000u);
     }
 };
 template <> struct Codec16<7> {   // P16_2C
@@ -288,14 +351,14 @@ template <> struct Codec16<7> {   // P16_2C
 template <> struct Codec16<8> {   // P16_0, unscaled
     static constexpr int SL = 0;
     __device__ static float dec_g(uint32_t c) { return posit_decode<0>(c, 0); }
-    __device__ static uint32_t enc_g(float g) { return p160_encode(g); }
+    __device__ static uint32_t enc_g(float g) { return posit_encode<0>(g); }
     __device__ static float dec(uint32_t c) { return dec_g(c); }
     __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
 template <> struct Codec16<9> {   // P16_1, unscaled
     static constexpr int SL = 0;
     __device__ static float dec_g(uint32_t c) { return posit_decode<1>(c, 0); }
-    __device__ static uint32_t enc_g(float g) { return p161_encode(g); }
+    __device__ static uint32_t enc_g(float g) { return posit_encode<1>(g); }
     __device__ static float dec(uint32_t c) { return dec_g(c); }
     __device__ static uint32_t enc(float x) { return enc_g(x); }
 };
@@ -476,15 +539,38 @@ __device__ __forceinline__ void moments(const R* g, R& rho, R* j, R sh) {
     j[2] = jsum<V, 2, 1, true, R>(g, R(0));
 }
 
-// u_a = (j_a + F_a/2) / rho (Sec. 2.2: each momentum component divided by
-// rho, u_x = (f1 - f2 + ...)/rho; Guo half-force), before clamping: one IEEE
-// division per component.  j is the scaled momentum; its 2^-SL is exact.
+// Velocity u_a = x_a / rho with x_a = j_a + F_a/2 (Sec. 2.2: each momentum
+// component divided by rho, u_x = (f1 - f2 + ...)/rho; Guo half-force), before
+// clamping: one IEEE division per component.  j is the scaled momentum; its
+// 2^-SL is exact.
 template <class R, int SL>
-__device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
+__device__ __forceinline__ void numerators(const Relax<R>& k, const R* j, R* x) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         const R jj = SL == 0 ? j[a] : j[a] * R(Pow2<SL>::down);
-        u[a] = (k.force ? fmaR(R(0.5), k.F[a], jj) : jj) / rho;
+        x[a] = k.force ? fmaR(R(0.5), k.F[a], jj) : jj;
+    }
+}
+
+template <class R, int SL>
+__device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
+    R x[3];
+    numerators<R, SL>(k, j, x);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = x[a] / rho;
+}
+
+// the same for two cells, so that the six divisions overlap
+template <class R, int SL>
+__device__ __forceinline__ void velocity_pair(const Relax<R>& k, R ra, const R* ja, R* ua, R rb, const R* jb,
+                                              R* ub) {
+    R xa[3], xb[3];
+    numerators<R, SL>(k, ja, xa);
+    numerators<R, SL>(k, jb, xb);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        ua[a] = xa[a] / ra;
+        ub[a] = xb[a] / rb;
     }
 }
 
@@ -530,14 +616,10 @@ __device__ __forceinline__ void guo_source(const Relax<R>& k, const R* u, const 
     });
 }
 
-// streamed populations g -> post-collision populations (in place), both 2^SL f
+// streamed populations g -> post-collision populations (in place), both
+// 2^SL f, given the density and the clamped velocity
 template <class V, int COLL, class R, int SL>
-__device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
-    R rho, j[3], u[3];
-    moments<V, R, SL>(f, rho, j, k.sh);
-    velocity<R, SL>(k, rho, j, u);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = minR(maxR(u[a], -k.cs), k.cs);
+__device__ __forceinline__ void collide_post(const Relax<R>& k, R* f, R rho, const R* u) {
     R feq[V::Q], Bp[V::Q], S[V::Q];
     equilibrium<V, R, SL>(rho, u, feq, Bp, k.sh);
     if (k.force) guo_source<V, R, SL>(k, u, Bp, S);
@@ -600,6 +682,38 @@ __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
             f[q] = fmaR(k.omm, sm, fmaR(-k.omp, sp, fq));
         });
     }
+}
+
+// each component clamped to [-cs, cs] (the paper's core limits |u_a| to c_s)
+template <class R>
+__device__ __forceinline__ void clamp_u(const Relax<R>& k, R* u) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a] = minR(maxR(u[a], -k.cs), k.cs);
+}
+
+// one stream-collide update: moments, velocity, clamp, equilibrium, collision
+template <class V, int COLL, class R, int SL>
+__device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
+    R rho, j[3], u[3];
+    moments<V, R, SL>(f, rho, j, k.sh);
+    velocity<R, SL>(k, rho, j, u);
+    clamp_u(k, u);
+    collide_post<V, COLL, R, SL>(k, f, rho, u);
+}
+
+// two cells: the density and velocity of both first, so that their
+// dependent chains (sums, reciprocal, corrections) overlap, then each cell's
+// equilibrium and collision; the same values as two collide() calls
+template <class V, int COLL, class R, int SL>
+__device__ __forceinline__ void collide_pair(const Relax<R>& k, R* fa, R* fb) {
+    R ra, rb, ja[3], jb[3], ua[3], ub[3];
+    moments<V, R, SL>(fa, ra, ja, k.sh);
+    moments<V, R, SL>(fb, rb, jb, k.sh);
+    velocity_pair<R, SL>(k, ra, ja, ua, rb, jb, ub);
+    clamp_u(k, ua);
+    clamp_u(k, ub);
+    collide_post<V, COLL, R, SL>(k, fa, ra, ua);
+    collide_post<V, COLL, R, SL>(k, fb, rb, ub);
 }
 
 template <class V, class R, int SL>

@@ -32,7 +32,10 @@ struct lbm_ensemble {
     uint32_t* tile_member = nullptr;
     size_t table_bytes = 0, tiles_alloc = 0;
     int total_tiles = 0;
-    int tile = 256;                 // cells per tile = threads per block
+    int tile = 256;                 // cells per tile (per-cell kernel: = threads per block)
+    int variant = LBM_ENS_PER_CELL; // LBM_ENS_PER_CELL or LBM_ENS_PAIRED
+    int warps = 4;                  // paired kernel: warps (runs of 64 cells) per tile
+    std::vector<uint32_t> open;     // per member: a face holds non-solid cells
     bool idx32 = true;              // every member's q*N < 2^32
     int64_t s = 0;                  // steps taken through the ensemble
     std::vector<int64_t> t0;        // member step counters at creation
@@ -51,6 +54,17 @@ struct lbm_ensemble {
 };
 
 namespace {
+
+// sets *out if a cell on a face of the lattice is not solid
+__global__ void k_face_open(const uint8_t* __restrict__ flags, int nx, int ny, int nz, int* out) {
+    const uint32_t plane = (uint32_t)nx * (uint32_t)ny, N = plane * (uint32_t)nz;
+    for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const uint32_t z = n / plane, r = n - z * plane, y = r / (uint32_t)nx, x = r - y * (uint32_t)nx;
+        const bool face = x == 0 || x + 1 == (uint32_t)nx || y == 0 || y + 1 == (uint32_t)ny || z == 0 ||
+                          z + 1 == (uint32_t)nz;
+        if (face && !(flags[n] & lbm::F_WALL)) atomicOr(out, 1);
+    }
+}
 
 __global__ void k_tag_cells(const uint32_t* __restrict__ cells, uint32_t count, uint32_t member, uint64_t* out) {
     for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x)
@@ -84,12 +98,16 @@ std::vector<EnsMember<R>> make_table(lbm_ensemble* e, std::vector<uint32_t>& til
         M.args[0] = h->args(rk, e->aa ? 0 : h->cur);
         M.args[1] = h->args(rk, e->aa ? 0 : 1 - h->cur);
         // L2 prefetch distance in tiles: the tiles that fit on the GPU at once
-        M.args[0].pf = M.args[1].pf = h->num_sms * (2048 / e->tile);
+        // (paired kernel: 20 warps per SM)
+        M.args[0].pf = M.args[1].pf =
+            e->variant == LBM_ENS_PAIRED ? h->num_sms * (20 / e->warps) : h->num_sms * (2048 / e->tile);
         M.ncells = (uint32_t)h->N;
         M.tile0 = total;
         M.by_plane = make_div((uint32_t)h->plane());
         M.by_nx = make_div((uint32_t)h->p.nx);
-        const uint32_t tiles = (uint32_t)((h->N + e->tile - 1) / e->tile);
+        M.open = e->open[k];
+        const uint32_t tile_cells = e->variant == LBM_ENS_PAIRED ? 64u * (uint32_t)e->warps : (uint32_t)e->tile;
+        const uint32_t tiles = (uint32_t)((h->N + tile_cells - 1) / tile_cells);
         tile_member.insert(tile_member.end(), tiles, (uint32_t)k);
         total += tiles;
     }
@@ -148,14 +166,16 @@ lbm_status upload_table(lbm_ensemble* e) {
 // kernel launch of ensemble step number `s` (0-based since creation)
 lbm_status launch(lbm_ensemble* e, int64_t s, cudaStream_t stream) {
     Launch L;
-    L.block = dim3(e->tile, 1, 1);
+    L.block = e->variant == LBM_ENS_PAIRED ? dim3(32, e->warps, 1) : dim3(e->tile, 1, 1);
     L.grid = dim3(e->total_tiles, 1, 1);
     L.stream = stream;
     const int64_t t = e->t0[0] + s;
     const int scheme = !e->aa ? SCHEME_AB : ((t & 1) ? SCHEME_AA_LOC : SCHEME_AA_PP);
     const int parity = e->aa ? 0 : (int)(s & 1);
-    lbm_status st = e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L),
-                            "ensemble kernel");
+    lbm_status st = e->variant == LBM_ENS_PAIRED
+                        ? e->cuda(e->ks->ens_pair(e->table, e->tile_member, parity, L), "paired ensemble kernel")
+                        : e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L),
+                                  "ensemble kernel");
     if (st != LBM_OK || e->n_list == 0) return st;
     Launch B;
     B.block = dim3(256, 1, 1);
@@ -223,6 +243,28 @@ extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count,
     if (cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking) != cudaSuccess) {
         delete e;
         return LBM_ERR_CUDA;
+    }
+    {   // which members have non-solid cells on a face (the paired kernel sends those through the per-cell path)
+        int* dev = nullptr;
+        if (cudaMalloc((void**)&dev, sizeof(int) * count) != cudaSuccess) {
+            lbm_ensemble_destroy(e);
+            return LBM_ERR_OOM;
+        }
+        cudaMemsetAsync(dev, 0, sizeof(int) * count, e->stream);
+        for (int k = 0; k < count; ++k) {
+            const lbm_handle* h = members[k];
+            k_face_open<<<(unsigned)std::min<size_t>((h->N + 255) / 256, 1024), 256, 0, e->stream>>>(
+                h->flags, h->p.nx, h->p.ny, h->p.nz, dev + k);
+        }
+        std::vector<int> host(count);
+        const cudaError_t ce = cudaMemcpyAsync(host.data(), dev, sizeof(int) * count, cudaMemcpyDeviceToHost, e->stream);
+        const cudaError_t se = cudaStreamSynchronize(e->stream);
+        cudaFree(dev);
+        if (ce != cudaSuccess || se != cudaSuccess) {
+            lbm_ensemble_destroy(e);
+            return LBM_ERR_CUDA;
+        }
+        e->open.assign(host.begin(), host.end());
     }
     const lbm_status st = upload_table(e);
     if (st != LBM_OK) {
@@ -299,16 +341,51 @@ extern "C" lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by) {
 }
 
 namespace {
+bool pair_ok(const lbm_ensemble* e) { return e->ks->ens_pair && !e->aa && e->idx32; }
+}  // namespace
 
-// times every tile size for the current scheme; returns the best (ms, tile)
-lbm_status time_tiles(lbm_ensemble* e, int trial_steps, float* best_ms, int* best_tile) {
+extern "C" lbm_status lbm_ensemble_set_variant(lbm_ensemble* e, int variant, int warps) {
+    if (!e) return LBM_ERR_ARG;
+    if (variant != LBM_ENS_PER_CELL && variant != LBM_ENS_PAIRED) return LBM_ERR_ARG;
+    if (variant == LBM_ENS_PAIRED && (warps < 1 || warps > 4)) return LBM_ERR_ARG;
+    lbm_status st = check_members(e);
+    if (st != LBM_OK) return st;
+    if (variant == LBM_ENS_PAIRED && !pair_ok(e)) {
+        e->err = "the paired ensemble kernel needs A-B streaming, FP16 or FP16S storage with FP32 arithmetic, "
+                 "SRT or TRT collision and q N < 2^32 for every member";
+        return LBM_ERR_UNSUPPORTED;
+    }
+    e->variant = variant;
+    if (variant == LBM_ENS_PAIRED) e->warps = warps;
+    return upload_table(e);
+}
+
+extern "C" int lbm_ensemble_get_variant(const lbm_ensemble* e) { return e ? e->variant : -1; }
+
+namespace {
+
+// One configuration of the ensemble launch: the per-cell kernel with a tile
+// size, or the paired kernel with warps per tile.
+struct EnsConfig {
+    int variant, size;
+};
+
+// times every configuration that applies to the current scheme; returns the best
+lbm_status time_configs(lbm_ensemble* e, int trial_steps, float* best_ms, EnsConfig* best) {
     static const int tiles[] = {256, 128, 64, 192, 96};
+    static const int warps[] = {4, 2, 1};
+    std::vector<EnsConfig> cfg;
+    for (int t : tiles) cfg.push_back({LBM_ENS_PER_CELL, t});
+    if (pair_ok(e))
+        for (int w : warps) cfg.push_back({LBM_ENS_PAIRED, w});
     cudaEvent_t ev[2];
     if (e->cuda(cudaEventCreate(&ev[0]), "event") || e->cuda(cudaEventCreate(&ev[1]), "event")) return LBM_ERR_CUDA;
     lbm_status st = LBM_OK;
     *best_ms = INFINITY;
-    for (int tile : tiles) {
-        st = lbm_ensemble_set_block(e, tile, 1);
+    for (const EnsConfig& c : cfg) {
+        st = c.variant == LBM_ENS_PAIRED ? lbm_ensemble_set_variant(e, LBM_ENS_PAIRED, c.size)
+                                         : lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0);
+        if (st == LBM_OK && c.variant == LBM_ENS_PER_CELL) st = lbm_ensemble_set_block(e, c.size, 1);
         if (st != LBM_OK) break;
         st = lbm_ensemble_step(e, 2);   // warm-up
         if (st != LBM_OK) break;
@@ -319,11 +396,17 @@ lbm_status time_tiles(lbm_ensemble* e, int trial_steps, float* best_ms, int* bes
         if (e->cuda(cudaEventSynchronize(ev[1]), "event sync")) { st = LBM_ERR_CUDA; break; }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, ev[0], ev[1]);
-        if (ms < *best_ms) { *best_ms = ms; *best_tile = tile; }
+        if (ms < *best_ms) { *best_ms = ms; *best = c; }
     }
     cudaEventDestroy(ev[0]);
     cudaEventDestroy(ev[1]);
     return st;
+}
+
+lbm_status apply_config(lbm_ensemble* e, const EnsConfig& c) {
+    if (c.variant == LBM_ENS_PAIRED) return lbm_ensemble_set_variant(e, LBM_ENS_PAIRED, c.size);
+    const lbm_status st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0);
+    return st != LBM_OK ? st : lbm_ensemble_set_block(e, c.size, 1);
 }
 
 // converts every member (lbm_set_scheme) and rebuilds the ensemble's tables
@@ -356,25 +439,29 @@ extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, in
     if (st != LBM_OK) return st;
     trial_steps += trial_steps & 1;       // whole A-A step pairs: the scheme may change between trials
     float ms0 = 0.f, ms1 = INFINITY;
-    int tile0 = e->tile, tile1 = e->tile;
-    st = time_tiles(e, trial_steps, &ms0, &tile0);
+    EnsConfig c0{LBM_ENS_PER_CELL, e->tile}, c1 = c0;
+    st = time_configs(e, trial_steps, &ms0, &c0);
     if (st != LBM_OK) return st;
     const int scheme0 = e->aa ? LBM_STREAM_AA : LBM_STREAM_AB;
     const int scheme1 = e->aa ? LBM_STREAM_AB : LBM_STREAM_AA;
     // the other streaming scheme, where every member allows it (A-A: no
     // outflow or free-slip cells) and the memory for A-B copies is there
     bool other = (scheme1 == LBM_STREAM_AB || can_use_aa(e)) && ((e->t0[0] + e->s) & 1) == 0;
-    if (other && switch_scheme(e, scheme1) == LBM_OK) {
-        st = time_tiles(e, trial_steps, &ms1, &tile1);
+    if (other && (st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) == LBM_OK && switch_scheme(e, scheme1) == LBM_OK) {
+        st = time_configs(e, trial_steps, &ms1, &c1);
         if (st != LBM_OK) return st;
-        if (ms0 <= ms1 && (st = switch_scheme(e, scheme0)) != LBM_OK) return st;
+        if (ms0 <= ms1) {
+            if ((st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) != LBM_OK) return st;
+            if ((st = switch_scheme(e, scheme0)) != LBM_OK) return st;
+        }
     } else {
+        if (st != LBM_OK) return st;
         other = false;
     }
-    const int tile = other && ms1 < ms0 ? tile1 : tile0;
-    st = lbm_ensemble_set_block(e, tile, 1);
-    if (bx_out) *bx_out = tile;
-    if (by_out) *by_out = 1;
+    const EnsConfig best = other && ms1 < ms0 ? c1 : c0;
+    st = apply_config(e, best);
+    if (bx_out) *bx_out = best.variant == LBM_ENS_PAIRED ? 64 * best.size : best.size;
+    if (by_out) *by_out = best.variant == LBM_ENS_PAIRED ? best.size : 1;
     return st;
 }
 

@@ -36,6 +36,8 @@ struct lbm_handle {
     double* partial = nullptr;
     int64_t t = 0;
     int cur = 0;
+    int64_t check_every = 0;   // lbm_set_divergence_check: steps between FP64 checks (0: off)
+    double check_tol = 0.0, check_mass0 = 0.0;
     int bx = 128, by = 2;
     int variant = 0;           // requested stream-collide kernel variant (LBM_VARIANT_*)
     int chunked = 0;           // populations in the chunked layout (flag-free A-B, 16-bit)

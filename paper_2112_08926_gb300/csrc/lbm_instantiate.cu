@@ -44,6 +44,13 @@ cudaError_t launch_ens(const void* members, const uint32_t* tile_member, int par
     return cudaGetLastError();
 }
 
+template <class V, int COLL>
+cudaError_t launch_ens_pair(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
+    k_ensemble_pair<V, COLL, FMT><<<L.grid, L.block, 0, L.stream>>>(
+        static_cast<const EnsMember<float>*>(members), tile_member, parity);
+    return cudaGetLastError();
+}
+
 template <class V, int COLL, int SCHEME, class IX>
 cudaError_t launch_ens_list(const void* members, const uint64_t* cells, uint32_t count, int parity, const Launch& L) {
     k_ensemble_list<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
@@ -133,6 +140,8 @@ void fill() {
             s.list_chunked[PH.value] = launch_list<V, COLL, PH.value, uint32_t, true>;
         });
     }
+    if constexpr (LBM_ARITH == 0 && (FMT == 2 || FMT == 3) && COLL < 2 && std::is_same<V, D3Q19>::value)
+        s.ens_pair = launch_ens_pair<V, COLL>;
     if constexpr (LBM_ARITH == 0 && FMT != 0 && COLL < 2 && std::is_same<V, D3Q19>::value) {
         s.staged[0] = launch_staged<V, COLL, 128>;
         s.staged[1] = launch_staged<V, COLL, 256>;

@@ -493,12 +493,22 @@ __global__ void __launch_bounds__(256, 3) k_step_pair(const StepArgs<float> a) {
         }
     });
     float f[V::Q];
-    static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] & 0xFFFFu); });
-    collide<V, COLL, float, SL>(a.k, f);
-    static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFF0000u) | C::enc_g(f[I.value]); });
-    static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] >> 16); });
-    collide<V, COLL, float, SL>(a.k, f);
-    static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFFu) | (C::enc_g(f[I.value]) << 16); });
+    if constexpr (FMT == 2 || FMT == 3) {   // hardware conversions: both cells at once
+        float fb[V::Q];
+        static_for<0, V::Q>([&](auto I) {
+            f[I.value] = C::dec_g(g[I.value] & 0xFFFFu);
+            fb[I.value] = C::dec_g(g[I.value] >> 16);
+        });
+        collide_pair<V, COLL, float, SL>(a.k, f, fb);
+        static_for<0, V::Q>([&](auto I) { g[I.value] = C::enc_g(f[I.value]) | (C::enc_g(fb[I.value]) << 16); });
+    } else {
+        static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] & 0xFFFFu); });
+        collide<V, COLL, float, SL>(a.k, f);
+        static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFF0000u) | C::enc_g(f[I.value]); });
+        static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] >> 16); });
+        collide<V, COLL, float, SL>(a.k, f);
+        static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFFu) | (C::enc_g(f[I.value]) << 16); });
+    }
     if (active) {
         uint16_t* dst = (uint16_t*)a.dst;
         const uint32_t n0 = (uint32_t)x0 + yo[1] + zo[1];
@@ -558,6 +568,14 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
     using PC = PairCodec<FMT>;
     constexpr int SL = Codec16<FMT>::SL;
     constexpr uint32_t CHE = (uint32_t)V::Q * CHUNK;     // codes per chunk
+    // posits: the encoding table of the block (4 KB), filled before any warp leaves
+    constexpr bool TAB = FMT >= 5 && FMT <= 9;
+    __shared__ EncEntry tab[TAB ? 512 : 1];
+    if constexpr (TAB) {
+        const int t = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+        for (int i = t; i < 512; i += nt) tab[i] = kEncTable<FMT>.e[i];
+        __syncthreads();
+    }
     const int lane = threadIdx.x;
     const uint32_t X = blockIdx.x, XT = (uint32_t)a.nx / CHUNK;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -659,26 +677,33 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
             }
         }
     }
-    // SEQ (27 populations): one cell at a time, the first cell's codes going
-    // back into g before the second is decoded, so that only one cell's
-    // values are live (the register budget of 27 code pairs); otherwise both
-    // cells are decoded and encoded as pairs
-    constexpr bool SEQ = V::Q > 19;
+    // SEQ: one cell at a time, the first cell's codes going back into g
+    // before the second is decoded, so that only one cell's values are live:
+    // for 27 populations (the register budget of 27 code pairs) and for the
+    // software codecs (FP16C, posits), whose conversions need registers of
+    // their own.  The formats with hardware conversion decode and encode both
+    // cells as pairs.
+    constexpr bool SEQ = V::Q > 19 || !(FMT == 2 || FMT == 3);
+    auto enc1 = [&](float v) -> uint32_t {
+        if constexpr (TAB) return enc_table(tab, v);
+        else return Codec16<FMT>::enc_g(v);
+    };
     float fa[V::Q], fb[SEQ ? 1 : V::Q];
-    static_for<0, V::Q>([&](auto I) { fa[I.value] = PC::dec(g[I.value]).x; });
-    collide<V, COLL, float, SL>(a.k, fa);
+    static_for<0, V::Q>([&](auto I) {
+        if constexpr (SEQ) fa[I.value] = Codec16<FMT>::dec_g(g[I.value] & 0xFFFFu);
+        else fa[I.value] = PC::dec(g[I.value]).x;
+    });
     if constexpr (SEQ) {
-        static_for<0, V::Q>([&](auto I) {
-            g[I.value] = (g[I.value] & 0xFFFF0000u) | Codec16<FMT>::enc_g(fa[I.value]);
-            fa[I.value] = PC::dec(g[I.value]).y;
-        });
         collide<V, COLL, float, SL>(a.k, fa);
         static_for<0, V::Q>([&](auto I) {
-            g[I.value] = (g[I.value] & 0xFFFFu) | (Codec16<FMT>::enc_g(fa[I.value]) << 16);
+            g[I.value] = (g[I.value] & 0xFFFF0000u) | enc1(fa[I.value]);
+            fa[I.value] = Codec16<FMT>::dec_g(g[I.value] >> 16);
         });
+        collide<V, COLL, float, SL>(a.k, fa);
+        static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFFu) | (enc1(fa[I.value]) << 16); });
     } else {
         static_for<0, V::Q>([&](auto I) { fb[I.value] = PC::dec(g[I.value]).y; });
-        collide<V, COLL, float, SL>(a.k, fb);
+        collide_pair<V, COLL, float, SL>(a.k, fa, fb);
     }
     // the new code pair of population i
     auto pair = [&](auto I) -> uint32_t {
@@ -743,6 +768,7 @@ template <class R> struct EnsMember {
     StepArgs<R> args[2];       // args[p]: arguments for a step of parity p
     uint32_t ncells, tile0;    // cells, first global tile of this member
     FastDiv by_plane, by_nx;
+    uint32_t open;             // a face of the lattice holds non-solid cells (periodic or open faces)
 };
 
 // L2 prefetch for the tile a.pf tiles further in launch order (about one
@@ -790,6 +816,141 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : (COLL == 2 ? 3 : 4))
     const uint32_t y = M.by_nx.div(r);
     const uint32_t x = r - y * (uint32_t)a.nx;
     cell_step<V, COLL, FMT, R, SCHEME, false, IX, true>(a, (int)x, (int)y, (int)z);
+}
+
+// Paired ensemble step, A-B, 16-bit storage with hardware conversion (FP16,
+// FP16S), FP32 arithmetic, members on the structure-of-arrays layout: one warp
+// per run of 64 consecutive cells of a member (lane l: cells 2l, 2l + 1 of
+// the run), every population moved as 32-bit pairs of codes.  Population i of
+// cell n streams from the cell n - d_i, d_i = c_ix + nx (c_iy + ny c_iz), which
+// is its upstream neighbour for every cell off the lattice's faces.  A source
+// pair that starts at an odd element is this lane's upper code and the next
+// lane's lower one (lane 31 reads the missing code); a destination pair at an
+// odd element (i N odd) is written as the word of the previous lane's upper
+// and this lane's lower code, with the codes that cross into the neighbouring
+// runs as single 16-bit stores.  Updated here: plain cells (flag byte 0) and
+// plain bounce-back cells (F_NEAR_SOLID) off the faces; in a member with
+// non-solid face cells those take the per-cell path; the listed cells follow
+// in k_ensemble_list.  Lanes without a cell to update read in-range elements
+// (clamped) and write nothing.
+// the per-cell update of a cell on a lattice face (wrapped neighbours), kept
+// out of line so that the paired kernel's registers serve its common path
+template <class V, int COLL, int FMT>
+__device__ __noinline__ void ensemble_face_cell(const StepArgs<float>& a, int x, int y, int z) {
+    cell_step<V, COLL, FMT, float, SCHEME_AB, false, uint32_t, true>(a, x, y, z);
+}
+
+template <class V, int COLL, int FMT>
+__global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>* __restrict__ members,
+                                                          const uint32_t* __restrict__ tile_member, int parity) {
+    using PC = PairCodec<FMT>;
+    constexpr int SL = Codec16<FMT>::SL;
+    const EnsMember<float>& M = members[__ldg(tile_member + blockIdx.x)];
+    const int lane = threadIdx.x;
+    const uint32_t run = (blockIdx.x - M.tile0) * blockDim.y + threadIdx.y;
+    const uint32_t N = M.ncells;
+    if (run * 64u >= N) return;                                   // whole warps leave
+    const StepArgs<float>& a = M.args[parity];                    // read in place (uniform loads)
+    // L2 prefetch of the run a.pf tiles further in launch order (about one
+    // wave later): its q population ranges and its flags, one line per lane
+    if constexpr (FMT == 2 || FMT == 3) {
+        const uint32_t ft = blockIdx.x + (uint32_t)a.pf;
+        if (a.pf > 0 && ft < gridDim.x) {
+            const EnsMember<float>& F = members[__ldg(tile_member + ft)];
+            const uint32_t fr = (ft - F.tile0) * blockDim.y + threadIdx.y;
+            if (fr * 64u < F.ncells) {
+                const uint16_t* fs = (const uint16_t*)F.args[parity].src;
+                if (lane < V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(fs + (size_t)lane * F.ncells + fr * 64u));
+                else if (lane == V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(F.args[parity].flags + fr * 64u));
+            }
+        }
+    }
+    const uint32_t n = run * 64u + 2u * (uint32_t)lane;          // the lane's first cell
+    const uint32_t f0 = n < N ? (uint32_t)a.flags[n] : F_WALL;
+    const uint32_t f1 = n + 1u < N ? (uint32_t)a.flags[n + 1u] : F_WALL;
+    uint32_t pl = (f0 == 0u ? 1u : 0u) | (f1 == 0u ? 2u : 0u);             // updated here: plain ...
+    uint32_t bb = (f0 == F_NEAR_SOLID ? 1u : 0u) | (f1 == F_NEAR_SOLID ? 2u : 0u);   // ... and bounce-back
+    const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
+    if (M.open && ((pl | bb) != 0u)) {
+        // cells on a face need wrapped neighbours: the per-cell path
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            if (!(((pl | bb) >> h) & 1u)) continue;
+            const uint32_t c = n + (uint32_t)h;
+            const uint32_t z = M.by_plane.div(c), r = c - z * plane, y = M.by_nx.div(r), x = r - y * (uint32_t)a.nx;
+            if (x == 0u || x + 1u == (uint32_t)a.nx || y == 0u || y + 1u == (uint32_t)a.ny || z == 0u ||
+                z + 1u == (uint32_t)a.nz) {
+                ensemble_face_cell<V, COLL, FMT>(a, (int)x, (int)y, (int)z);
+                pl &= ~(1u << h);
+                bb &= ~(1u << h);
+            }
+        }
+    }
+    if (!__any_sync(0xffffffffu, (pl | bb) != 0u)) return;
+    const uint16_t* src = (const uint16_t*)a.src;
+    uint16_t* dst = (uint16_t*)a.dst;
+    const uint32_t qN2 = (uint32_t)V::Q * N - 2u;                 // last even element start
+    uint32_t g[V::Q];
+    static_for<0, V::Q>([&](auto I) {
+        constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
+        const int32_t d = cx + cy * a.nx + cz * (int32_t)plane;
+        const uint32_t e = (uint32_t)i * N + n - (uint32_t)d;     // element of the first cell's source
+        const uint32_t es = min(e & ~1u, qN2);
+        const uint32_t w = *reinterpret_cast<const uint32_t*>(src + es);
+        if ((((uint32_t)i * N - (uint32_t)d) & 1u) == 0u) {        // warp-uniform
+            g[i] = w;
+        } else {                                                    // codes e, e + 1: hi of w, lo of the next word
+            uint32_t nxt = __shfl_down_sync(0xffffffffu, w, 1);
+            if (lane == 31) nxt = (uint32_t)src[min(es + 2u, qN2 + 1u)];
+            g[i] = __byte_perm(w, nxt, 0x5432);
+        }
+    });
+    // plain bounce-back: a direction whose upstream cell is solid takes the
+    // code of the cell's own opposite population
+    if (__any_sync(0xffffffffu, bb != 0u)) {
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {
+            if (!((bb >> h) & 1u)) continue;
+            const uint32_t c = n + (uint32_t)h;
+            const uint32_t z = M.by_plane.div(c), r = c - z * plane, y = M.by_nx.div(r), x = r - y * (uint32_t)a.nx;
+            const Nbr nb((int)x, (int)y, (int)z, a.nx, a.ny, a.nz);
+            const uint32_t walls = solid_upstream<V>(a.flags, nb);
+            static_for<1, V::Q>([&](auto I) {
+                constexpr int i = I.value;
+                if ((walls >> i) & 1u) {
+                    const uint32_t cc = src[(uint32_t)opposite(i) * N + c];
+                    g[i] = h ? ((g[i] & 0xFFFFu) | (cc << 16)) : ((g[i] & 0xFFFF0000u) | cc);
+                }
+            });
+        }
+    }
+    float fa[V::Q], fb[V::Q];
+    static_for<0, V::Q>([&](auto I) {
+        const float2 v = PC::dec(g[I.value]);
+        fa[I.value] = v.x;
+        fb[I.value] = v.y;
+    });
+    collide_pair<V, COLL, float, SL>(a.k, fa, fb);
+    const uint32_t ok = pl | bb;
+    const uint32_t ok_up = __shfl_up_sync(0xffffffffu, ok, 1);
+    static_for<0, V::Q>([&](auto I) {
+        constexpr int i = I.value;
+        const uint32_t own = PC::enc(fa[i], fb[i]);
+        const uint32_t e = (uint32_t)i * N + n;
+        if ((((uint32_t)i * N) & 1u) == 0u) {                      // warp-uniform: aligned pair
+            if (ok == 3u) *reinterpret_cast<uint32_t*>(dst + e) = own;
+            else if (ok == 1u) dst[e] = (uint16_t)own;
+            else if (ok == 2u) dst[e + 1u] = (uint16_t)(own >> 16);
+        } else {                                                    // word e-1: previous lane's upper, own lower code
+            const uint32_t up = __shfl_up_sync(0xffffffffu, own, 1);
+            const uint32_t okw = (lane == 0 ? 0u : ((ok_up >> 1) & 1u)) | ((ok & 1u) << 1);
+            const uint32_t w = __byte_perm(up, own, 0x5432);
+            if (okw == 3u) *reinterpret_cast<uint32_t*>(dst + e - 1u) = w;
+            else if (okw == 2u) dst[e] = (uint16_t)own;
+            else if (okw == 1u) dst[e - 1u] = (uint16_t)(up >> 16);
+            if (lane == 31 && (ok & 2u)) dst[e + 1u] = (uint16_t)(own >> 16);   // cell n + 1: the next run's word
+        }
+    });
 }
 
 // The non-plain cells of all members: entry = member << 32 | cell.

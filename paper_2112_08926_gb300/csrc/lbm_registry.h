@@ -29,6 +29,7 @@ struct KernelSet {
     ListFn list_chunked[3] = {}; // [scheme]: the same on the chunked layout
     EnsFn ens[3][2] = {};        // [scheme][32-bit indices], flags always on: plain cells
     EnsListFn ens_list[3][2] = {};   // the listed non-plain cells of all members
+    EnsFn ens_pair = nullptr;    // paired ensemble step (A-B, 32-bit indices, FP16 / FP16S, D3Q19)
     ProbeFn probe[8] = {};    // [layout code: phase | 4 if chunked]
     PutFn put[4] = {};        // [bit 0: A-A, bit 1: chunked]
     StagedFn staged[3] = {};  // row length 128, 256, 512 (D3Q19, FP32 arithmetic only)

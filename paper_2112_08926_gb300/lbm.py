@@ -42,7 +42,8 @@ EXPORTS = [
     "lbm_ensemble_set_block", "lbm_ensemble_autotune", "lbm_ensemble_destroy",
     "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant", "lbm_get_rho_u_static",
     "lbm_set_nodes", "lbm_get_f_cells", "lbm_get_rho_u_cells", "lbm_selftest_wait_timeout",
-    "lbm_set_scheme", "lbm_ensemble_scheme",
+    "lbm_set_scheme", "lbm_ensemble_scheme", "lbm_set_divergence_check", "lbm_codec_encode_bits_table",
+    "lbm_ensemble_set_variant", "lbm_ensemble_get_variant",
 ]
 
 
@@ -102,6 +103,7 @@ def load() -> ctypes.CDLL:
             "lbm_set_geometry": [P, P, P, P],
             "lbm_set_rho_u": [P, P, P, P, P],
             "lbm_step": [P, I64],
+            "lbm_set_divergence_check": [P, I64, D],
             "lbm_get_rho_u": [P, P, P, P, P],
             "lbm_get_rho_u_static": [P, P, P, P, P],
             "lbm_get_f": [P, P],
@@ -119,10 +121,13 @@ def load() -> ctypes.CDLL:
             "lbm_codec_encode": [I, P, P, I64, P],
             "lbm_codec_decode": [I, P, P, I64, P],
             "lbm_codec_encode_bits": [I, ctypes.c_uint32, I64, P, P],
+            "lbm_codec_encode_bits_table": [I, ctypes.c_uint32, I64, P, P],
             "lbm_ensemble_create": [ctypes.POINTER(P), I, ctypes.POINTER(P)],
             "lbm_ensemble_step": [P, I64],
             "lbm_ensemble_step_each": [P, I64],
             "lbm_ensemble_set_block": [P, I, I],
+            "lbm_ensemble_set_variant": [P, I, I],
+            "lbm_ensemble_get_variant": [P],
             "lbm_ensemble_autotune": [P, I, pI, pI],
             "lbm_ensemble_destroy": [P],
             "lbm_set_variant": [P, I],
@@ -311,6 +316,12 @@ class Lattice:
     def step(self, n=1):
         self._c(self._L.lbm_step(self._h, int(n)))
 
+    def set_divergence_check(self, every, mass_tol=0.0):
+        """FP64 check inside step() every `every` steps (0: off): raises
+        LBMError(LBM_ERR_DIVERGED) on a non-finite state or a relative mass
+        drift above mass_tol (lbm_set_divergence_check)."""
+        self._c(self._L.lbm_set_divergence_check(self._h, int(every), float(mass_tol)))
+
     def rho_u(self):
         out = [np.empty(self.N, dtype=np.float64) for _ in range(4)]
         self._c(self._L.lbm_get_rho_u(self._h, *[_ptr(a) for a in out]))
@@ -389,8 +400,18 @@ class Ensemble:
     def set_block(self, bx, by):
         _check(self._L.lbm_ensemble_set_block(self._e, int(bx), int(by)), self._e, ensemble=True)
 
+    def set_variant(self, variant, warps=4):
+        """'per_cell' or 'paired' (two cells per thread, `warps` runs of 64
+        cells per tile); see lbm_ensemble_set_variant."""
+        code = {"per_cell": 0, "paired": 1}[variant]
+        _check(self._L.lbm_ensemble_set_variant(self._e, code, int(warps)), self._e, ensemble=True)
+
+    def variant(self) -> str:
+        return {0: "per_cell", 1: "paired"}[self._L.lbm_ensemble_get_variant(self._e)]
+
     def autotune(self, trial_steps=5):
-        """Picks tile size and streaming scheme; returns (tile, 1)."""
+        """Picks kernel, tile and streaming scheme; returns (cells per tile,
+        1 for the per-cell kernel or warps per tile of the paired one)."""
         bx, by = ctypes.c_int(), ctypes.c_int()
         _check(self._L.lbm_ensemble_autotune(self._e, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)),
                self._e, ensemble=True)
@@ -426,12 +447,14 @@ def codec_decode(storage, codes, out=None, stream=None):
     return out
 
 
-def codec_encode_bits(storage, first, n, out=None, stream=None, device=None):
+def codec_encode_bits(storage, first, n, out=None, stream=None, device=None, table=False):
+    """Codes of the floats with bit patterns first .. first+n-1; table=True
+    uses the paired kernel's table-driven posit encoder."""
     torch = _torch()
     if out is None:
         out = torch.empty(n, dtype=torch.int16, device=device or "cuda")
-    st = load().lbm_codec_encode_bits(STORAGES[storage], ctypes.c_uint32(first), int(n),
-                                      ctypes.c_void_p(out.data_ptr()),
-                                      ctypes.c_void_p(stream or current_stream_ptr()))
+    fn = load().lbm_codec_encode_bits_table if table else load().lbm_codec_encode_bits
+    st = fn(STORAGES[storage], ctypes.c_uint32(first), int(n), ctypes.c_void_p(out.data_ptr()),
+            ctypes.c_void_p(stream or current_stream_ptr()))
     _check(st)
     return out

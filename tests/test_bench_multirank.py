@@ -57,7 +57,7 @@ def test_single_process_needs_no_collective():
 def _run_reference(rank, world):
     env = dict(os.environ, RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
     return subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
-                           "--gpus", str(world), "--steps", "2", "--warmup", "3"],
+                           "--gpus", str(world), "--steps", "2", "--warmup", "3", "--size", "64"],
                           capture_output=True, text=True, env=env, timeout=600, cwd=ROOT)
 
 

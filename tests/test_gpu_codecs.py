@@ -51,6 +51,22 @@ def test_encode_all_fp32_inputs(fmt):
                         f"{first + int(k):#010x}: gpu {got[k]:#06x} oracle {ref[k]:#06x}")
 
 
+@pytest.mark.parametrize("fmt", ["P16_0S", "P16_1S", "P16_2C", "P16_0", "P16_1"])
+def test_table_encoder_all_fp32_inputs(fmt):
+    """The paired kernel's table-driven posit encoder, over all 2^32 inputs."""
+    import paper_2112_08926_gb300 as P
+    out = torch.empty(CHUNK, dtype=torch.int16, device="cuda")
+    for first in range(0, 1 << 32, CHUNK):
+        P.codec_encode_bits(fmt, first, CHUNK, out=out, table=True)
+        got = out.cpu().numpy().view(np.uint16)
+        ref = oracle.encode_bits_range(fmt, first, CHUNK)
+        mism = np.flatnonzero(got != ref)
+        if mism.size:
+            k = mism[0]
+            pytest.fail(f"{fmt}: {mism.size} mismatches in chunk {first:#x}, first at bits "
+                        f"{first + int(k):#010x}: gpu {got[k]:#06x} oracle {ref[k]:#06x}")
+
+
 @pytest.mark.parametrize("fmt", FORMATS)
 def test_decode_all_codes(fmt):
     import paper_2112_08926_gb300 as P

@@ -48,6 +48,79 @@ def test_ensemble_equals_per_member_launches(scheme):
         assert np.array_equal(ga.f(), gb.f())
 
 
+@pytest.mark.parametrize("storage,coll", [("FP16S", "SRT"), ("FP16", "TRT")])
+def test_paired_ensemble_equals_per_member_launches(storage, coll):
+    """The paired ensemble kernel (two cells per thread, 32-bit code pairs,
+    runs of 64 linear cells) on cavities of odd and even edges (every parity
+    of source and destination pairs), with 1, 2 and 4 runs per tile, against
+    one launch per member."""
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=9, n_min=5, n_max=23, seed=7)
+
+    def members():
+        out = []
+        for s in specs:
+            g = P.Lattice(s.n, s.n, s.n, "D3Q19", coll, storage, "FP32", "AB", tau=s.tau)
+            flags, node_u = W.cavity(s.n, s.u_lid)
+            g.set_geometry(flags, node_u)
+            g.set_rho_u(*W.random_fields((s.n, s.n, s.n), seed=s.n))
+            out.append(g)
+        return out
+
+    a, b = members(), members()
+    ea, eb = P.Ensemble(a), P.Ensemble(b)
+    for warps in (4, 1, 2):
+        ea.set_variant("paired", warps)
+        assert ea.variant() == "paired"
+        ea.step(70)          # a graph replay of 64 steps and 6 single launches
+        eb.step_each(70)
+        for ga, gb in zip(a, b):
+            assert np.array_equal(ga.f(), gb.f()), warps
+
+
+def test_paired_ensemble_open_faces_and_every_cell_kind():
+    """Members whose faces hold fluid cells (periodic in every direction) and
+    every kind of boundary cell: the face cells take the per-cell path inside
+    the paired launch, the listed cells the list launch; the result equals
+    one launch per member bit for bit."""
+    import paper_2112_08926_gb300 as P
+    shapes = [(7, 9, 11), (6, 10, 64), (5, 5, 33), (12, 3, 17)]
+
+    def members():
+        out = []
+        for k, shp in enumerate(shapes):
+            nz, ny, nx = shp
+            g = P.Lattice(nx, ny, nz, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=0.7, force=(1e-5, 0.0, -2e-5))
+            g.set_geometry(*W.random_geometry(shp, 40 + k))
+            g.set_rho_u(*W.random_fields(shp, seed=50 + k))
+            out.append(g)
+        return out
+
+    a, b = members(), members()
+    ea, eb = P.Ensemble(a), P.Ensemble(b)
+    ea.set_variant("paired", 2)
+    ea.step(70)
+    eb.step_each(70)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
+
+
+def test_paired_ensemble_members_match_oracle():
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=3, n_min=5, n_max=12, seed=98)
+    mem = make_members(specs, "FP16S", "AB", P)
+    e = P.Ensemble(mem)
+    e.set_variant("paired", 4)
+    e.step(70)
+    for s, g in zip(specs, mem):
+        o = oracle.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", "ORD32", "FP16S", tau=s.tau)
+        flags, node_u = W.cavity(s.n, s.u_lid)
+        o.set_geometry(flags, node_u)
+        o.set_rho_u()
+        o.step(70)
+        assert np.array_equal(g.f(), o.f())
+
+
 def test_ensemble_members_match_oracle():
     import paper_2112_08926_gb300 as P
     specs = W.ensemble_cavities(count=3, n_min=5, n_max=12, seed=99)

@@ -60,3 +60,61 @@ def test_bounded_wait_runs_out_and_is_reported():
 def test_null_handle_is_rejected():
     import paper_2112_08926_gb300 as P
     assert P.load().lbm_selftest_wait_timeout(ctypes.c_void_p(0)) == 1
+
+
+LBM_ERR_DIVERGED = 5
+
+
+@pytest.mark.parametrize("storage,arith,shape", [("FP32", "FP32", (6, 7, 9)), ("FP16S", "FP32", (8, 8, 64)),
+                                                 ("FP64", "FP64", (5, 6, 7))])
+def test_divergence_check_in_step_finds_an_injected_nan(storage, arith, shape):
+    """The failure is made on the host: one population of one cell is set to
+    NaN through lbm_set_f.  With the check on every 10 steps, lbm_step stops
+    at the first check after the NaN has entered (step 10) with
+    LBM_ERR_DIVERGED; the handle stays usable.  A run with the check on and no
+    fault gives bit for bit the populations of a run without it."""
+    import paper_2112_08926_gb300 as P
+    nz, ny, nx = shape
+    fields = W.random_fields(shape, seed=5)
+    ref = P.Lattice(nx, ny, nz, "D3Q19", "SRT", storage, arith, "AB", tau=0.7)
+    ref.set_rho_u(*fields)
+    ref.step(40)
+    chk = P.Lattice(nx, ny, nz, "D3Q19", "SRT", storage, arith, "AB", tau=0.7)
+    chk.set_rho_u(*fields)
+    chk.set_divergence_check(10, 1e-6)
+    chk.step(17)
+    chk.step(23)
+    assert np.array_equal(chk.f(), ref.f())
+    ref.close()
+    f = chk.f()
+    f[3, nz // 2, ny // 2, nx // 2] = np.nan
+    chk.set_f(f)                       # resets the step counter to 0
+    with pytest.raises(P.LBMError) as e:
+        chk.step(25)
+    assert e.value.status == LBM_ERR_DIVERGED
+    assert b"step 10" in chk._L.lbm_last_error(chk.handle)
+    assert chk.info().step == 10
+    chk.set_divergence_check(0)        # off: the handle still steps
+    chk.step(1)
+    chk.close()
+
+
+def test_divergence_check_finds_a_mass_jump():
+    """Mass drift beyond the tolerance counts as divergence: the populations
+    of one cell get a large positive offset (injected through lbm_set_f
+    after the check was set)."""
+    import paper_2112_08926_gb300 as P
+    shape = (6, 7, 9)
+    g = P.Lattice(9, 7, 6, "D3Q19", "SRT", "FP32", "FP32", "AB", tau=0.7)
+    g.set_rho_u(*W.random_fields(shape, seed=6))
+    g.set_divergence_check(4, 1e-6)
+    g.step(8)
+    f = g.f()
+    f[:, 2, 3, 4] += 0.01
+    g.set_f(f)
+    with pytest.raises(P.LBMError) as e:
+        g.step(8)
+    assert e.value.status == LBM_ERR_DIVERGED
+    g.set_divergence_check(4, 0.0)     # finiteness only: passes
+    g.step(8)
+    g.close()

@@ -70,7 +70,7 @@ def test_static_readback_refuses_planes_beyond_the_buffer():
     g = P.Lattice(1024, 257, 1, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=0.7)
     g.set_rho_u()
     st, _ = _read(lib, g, "lbm_get_rho_u_static")
-    assert st == P.LBM_ERR_UNSUPPORTED
+    assert st == P.lbm.LBM_ERR_UNSUPPORTED
     assert b"262144" in lib.lbm_last_error(g.handle)
     g.close()
 
@@ -82,9 +82,9 @@ def test_static_readback_reports_a_wait_that_gave_up():
     lib = P.load()
     g = P.Lattice(16, 8, 4, "D3Q19", "SRT", "FP32", "FP32", "AB", tau=0.7)
     g.set_rho_u()
-    assert lib.lbm_selftest_wait_timeout(g.handle) == P.LBM_ERR_TIMEOUT
+    assert lib.lbm_selftest_wait_timeout(g.handle) == P.lbm.LBM_ERR_TIMEOUT
     st, _ = _read(lib, g, "lbm_get_rho_u_static")
-    assert st in (P.LBM_ERR_TIMEOUT, P.LBM_ERR_STATE)
+    assert st in (P.lbm.LBM_ERR_TIMEOUT, P.lbm.LBM_ERR_STATE)
     g.close()
 
 
