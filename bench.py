@@ -257,7 +257,7 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
     mem = build()
     e = P.Ensemble(mem)
     bx, by = e.autotune(trial_steps=3)
-    scheme, kernel = e.scheme(), e.variant()
+    scheme, kernel, layout = e.scheme(), e.variant(), e.layout()
     e.step(warmup)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
     torch.cuda.synchronize()
@@ -278,8 +278,8 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
     peak, _ = peaks()
     bpc = 2 * 19 * 2 + 1   # 16-bit populations read and written, own flag byte
     return {"workload": f"{count} D3Q19 SRT lid-driven cavities, edges U{{16..128}} (splitmix64 seed {seed}), "
-                        f"tau U[0.51,0.9], lid U[0.02,0.1], FP32/FP16S, kernel, tile and streaming scheme autotuned",
-            "cells": cells, "steps": steps, "tile": [bx, by], "scheme": scheme, "kernel": kernel,
+                        f"tau U[0.51,0.9], lid U[0.02,0.1], FP32/FP16S, member layout, kernel, tile and streaming scheme autotuned",
+            "cells": cells, "steps": steps, "tile": [bx, by], "scheme": scheme, "kernel": kernel, "layout": layout,
             "batched_mlups": cells * steps / t_b / 1e6, "per_launch_mlups": cells * steps / t_e / 1e6,
             "bytes_per_cell": bpc, "frac_hbm": bpc * cells * steps / t_b / 1e9 / peak,
             "per_launch_frac_hbm": bpc * cells * steps / t_e / 1e9 / peak,

@@ -65,8 +65,12 @@ enum {
 /* arithmetic precision of the collision (the "FPa" of the paper's "FPa/FPs") */
 enum { LBM_ARITH_FP32 = 0, LBM_ARITH_FP64 = 1 };
 /* streaming scheme: one-step pull with two copies (A-B, Sec. 5) or the
- * in-place A-A scheme with one copy (Sec. 1 "any swap algorithm") */
-enum { LBM_STREAM_AB = 0, LBM_STREAM_AA = 1 };
+ * in-place A-A scheme with one copy (Sec. 1 "any swap algorithm").  AUTO (a
+ * creation parameter only): A-B when both copies fit in the device's free
+ * memory with a 10% margin, else A-A; lbm_autotune then also times the
+ * other scheme where the lattice allows it.  lbm_get_info reports the
+ * scheme in use. */
+enum { LBM_STREAM_AB = 0, LBM_STREAM_AA = 1, LBM_STREAM_AUTO = 2 };
 
 /* cell flag bits (one byte per cell) */
 #define LBM_FLUID        0x00u
@@ -84,7 +88,7 @@ typedef struct {
                            FP32/FP16S and FP32/FP16C; others LBM_ERR_UNSUPPORTED) */
     int storage;        /* LBM_FP64 .. LBM_P16_1 */
     int arith;          /* LBM_ARITH_FP32; LBM_ARITH_FP64 only with FP64/FP32 storage */
-    int scheme;         /* LBM_STREAM_AB, LBM_STREAM_AA */
+    int scheme;         /* LBM_STREAM_AB, LBM_STREAM_AA, LBM_STREAM_AUTO */
     double tau;         /* relaxation time (> 0.5); omega = 1/tau (appendix, SRT) */
     double trt_lambda;  /* TRT magic parameter (tau+ - 1/2)(tau- - 1/2), e.g. 3/16 */
     double force[3];    /* Guo body force per volume (Sec. 4.1); D2Q9 ignores z */
@@ -242,6 +246,7 @@ typedef struct {
     size_t device_bytes;      /* bytes held on the device */
     void* ddf[2];             /* device population copies (ddf[1] NULL for A-A) */
     int layout;               /* LBM_LAYOUT_SOA or LBM_LAYOUT_CHUNKED */
+    int scheme;               /* LBM_STREAM_AB or LBM_STREAM_AA (in use) */
 } lbm_info;
 
 lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info);
@@ -288,10 +293,13 @@ lbm_status lbm_set_scheme(lbm_handle* h, int scheme);
  * PAIRED (on the chunked layout where nx is a multiple of 64), STAGED -- and
  * keeps the fastest (its layout with it; query it with lbm_get_variant);
  * then, for the kernels that take one (GENERIC, PAIRED on the structure of
- * arrays), the thread-block shape, returned in *bx, *by.  Every variant and
- * shape gives the same values; the trial steps advance the lattice.  The
- * streaming scheme stays as it is (lbm_set_scheme switches it).  Trial runs
- * of 64 steps or more include one CUDA-graph capture (see lbm_step). */
+ * arrays), the thread-block shape, returned in *bx, *by; for a lattice created
+ * with LBM_STREAM_AUTO, first the streaming scheme (A-B against in-place A-A,
+ * switched with lbm_set_scheme where the step count is even, the lattice
+ * has no OUTFLOW or FREESLIP cells and memory for the second copy is there).
+ * Every choice gives the same values; the trial steps advance the lattice.
+ * Otherwise the scheme stays as it is.  Trial runs of 64 steps or more
+ * include one CUDA-graph capture (see lbm_step). */
 lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx, int* by);
 
 /* Self-test of the failure path (the paper has no counterpart): launches
@@ -355,12 +363,25 @@ lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by);
 enum { LBM_ENS_PER_CELL = 0, LBM_ENS_PAIRED = 1 };
 lbm_status lbm_ensemble_set_variant(lbm_ensemble* e, int variant, int warps);
 int lbm_ensemble_get_variant(const lbm_ensemble* e);
-/* Picks the kernel, its tile and the streaming scheme: times trial_steps
- * steps (rounded up to even) for every tile size of the per-cell kernel and,
- * where it applies, every tile of the paired kernel; then, where every member
- * allows it (A-A: no OUTFLOW or FREESLIP cells; memory for the A-B copies)
- * and the step count is even, converts all members to the other scheme
- * (lbm_set_scheme) and times again; keeps the fastest combination.  *bx
+/* Layout of the members' populations: LBM_LAYOUT_SOA (the default) or
+ * LBM_LAYOUT_CHUNKED, the array of structures of arrays of chunks of 64
+ * consecutive cells of the member's linear cell index (any nx; 16-bit
+ * storage, FP32 arithmetic, SRT or TRT, q N < 2^32).  The members are
+ * converted in place (no change in values); stepped on their own (also by
+ * lbm_ensemble_step_each) they use kernels with the same addressing.
+ * Destroying the ensemble returns them to the layout of their own settings.
+ * Both kernels of lbm_ensemble_set_variant take either layout.  Errors:
+ * LBM_ERR_ARG, LBM_ERR_UNSUPPORTED, LBM_ERR_OOM (A-A members convert through
+ * a transient copy). */
+lbm_status lbm_ensemble_set_layout(lbm_ensemble* e, int layout);
+int lbm_ensemble_get_layout(const lbm_ensemble* e);
+/* Picks the members' layout, the kernel, its tile and the streaming scheme:
+ * for each layout that applies (structure of arrays; chunked) times
+ * trial_steps steps (rounded up to even) for every tile size of the per-cell
+ * kernel and, where it applies, every tile of the paired kernel; then, where
+ * every member allows it (A-A: no OUTFLOW or FREESLIP cells; memory for the
+ * A-B copies) and the step count is even, converts all members to the other
+ * scheme (lbm_set_scheme) and times again; keeps the fastest combination.  *bx
  * receives the cells per tile, *by 1 for the per-cell kernel or the warps per
  * tile of the paired one.  The trial steps are real steps (two warm-up steps
  * per configuration on top).  Results do not depend on any of the choices. */

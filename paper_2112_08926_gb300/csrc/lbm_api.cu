@@ -167,7 +167,7 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
     if (p.collision == LBM_MRT && p.velset != LBM_D3Q19) return LBM_ERR_UNSUPPORTED;
     if (p.storage < LBM_FP64 || p.storage > LBM_P16_1) return LBM_ERR_ARG;
     if (p.arith != LBM_ARITH_FP32 && p.arith != LBM_ARITH_FP64) return LBM_ERR_ARG;
-    if (p.scheme != LBM_STREAM_AB && p.scheme != LBM_STREAM_AA) return LBM_ERR_ARG;
+    if (p.scheme != LBM_STREAM_AB && p.scheme != LBM_STREAM_AA && p.scheme != LBM_STREAM_AUTO) return LBM_ERR_ARG;
     if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return LBM_ERR_ARG;
     if (p.collision == LBM_TRT && !(p.trt_lambda > 0.0 && std::isfinite(p.trt_lambda))) return LBM_ERR_ARG;
     for (int a = 0; a < 3; ++a)
@@ -179,6 +179,14 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
 
     lbm_handle* h = new lbm_handle;
     h->p = p;
+    if (p.scheme == LBM_STREAM_AUTO) {   // A-B when both copies fit with a 10% margin
+        h->scheme_auto = true;
+        size_t free_b = 0, total_b = 0;
+        const double need = 2.0 * (double)velset_q(p.velset) * (double)N * storage_bytes(p.storage);
+        const bool fits = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && need * 1.1 < (double)free_b;
+        if (!fits) cudaGetLastError();
+        h->p.scheme = fits ? LBM_STREAM_AB : LBM_STREAM_AA;
+    }
     if (p.velset == LBM_D2Q9) h->p.force[2] = 0.0;
     if (p.collision == LBM_SRT) h->p.trt_lambda = p.trt_lambda > 0 ? p.trt_lambda : 0.1875;
     h->q = velset_q(p.velset);
@@ -195,7 +203,7 @@ extern "C" lbm_status lbm_create(const lbm_params* params, const lbm_allocator* 
     make_relax(h->p, h->kf);
     make_relax(h->p, h->kd);
 
-    const size_t fbytes = (size_t)h->q * N * h->sb;
+    const size_t fbytes = h->fbytes();
     const int copies = h->aa() ? 1 : 2;
     for (int c = 0; c < copies; ++c) {
         h->f[c] = h->alloc(fbytes);
@@ -478,7 +486,7 @@ namespace {
 // `upload(z0, z1, dev)` stages the chunk's input doubles into dev
 template <class R, class Up>
 lbm_status put_all(lbm_handle* h, const Relax<R>& k, int setf, int per_cell, Up upload) {
-    const size_t fbytes = (size_t)h->q * h->N * h->sb;
+    const size_t fbytes = h->fbytes();
     ++h->gen;
     for (int c = 0; c < (h->aa() ? 1 : 2); ++c)
         if (h->cuda(cudaMemsetAsync(h->f[c], 0, fbytes, h->stream), "memset")) return LBM_ERR_CUDA;
@@ -565,6 +573,7 @@ bool chunk_eligible(const lbm_handle* h) {
     return !h->fp64() && h->sb == 2 && (h->p.nx % lbm::CHUNK) == 0 && h->ks->pair_chunked[0][0];
 }
 bool want_chunked(const lbm_handle* h) {
+    if (h->force_chunked && !h->fp64() && h->sb == 2 && h->ks->step_ch[0]) return true;
     return chunk_eligible(h) && (h->variant == LBM_VARIANT_AUTO || h->variant == LBM_VARIANT_PAIRED);
 }
 
@@ -630,7 +639,7 @@ lbm_status ensure_layout(lbm_handle* h) {
     if (want == h->chunked) return LBM_OK;
     ++h->gen;
     // A-B: into the other copy; A-A (one copy): through a transient copy of it
-    const size_t fbytes = (size_t)h->q * h->N * h->sb;
+    const size_t fbytes = h->fbytes();
     TempBuffer tmp(h, h->aa() ? fbytes : 0);
     if (h->aa()) {
         if (!tmp.p) return h->fail(LBM_ERR_OOM, "relayout buffer");
@@ -654,7 +663,18 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
     StepArgs<R> a = h->args(k, h->aa() ? 0 : h->cur);
     const int variant = variant_in_use(h);
     lbm_status st;
-    if (h->chunked) {
+    if (h->chunked && (h->p.nx % lbm::CHUNK) != 0) {
+        // chunked layout forced by an ensemble on rows that are not whole
+        // chunks: the generic kernel with chunked addressing, then the list
+        st = h->cuda(h->ks->step_ch[scheme](&a, h->step_launch(s)), "step kernel");
+        if (st == LBM_OK && h->flags && h->n_complex > 0) {
+            Launch B;
+            B.block = dim3(256);
+            B.grid = dim3((h->n_complex + 255) / 256);
+            B.stream = s;
+            st = h->cuda(h->ks->list_chunked[scheme](&a, h->special, h->n_complex, B), "list kernel");
+        }
+    } else if (h->chunked) {
         Launch L;
         L.block = dim3(32, 8, 1);
         L.grid = dim3(h->p.nx / lbm::CHUNK, (h->p.ny + 7) / 8, h->p.nz);
@@ -711,6 +731,7 @@ template <class R> lbm_status launch_one_step(lbm_handle* h, const Relax<R>& k, 
 }  // namespace
 
 lbm_status lbm_internal_check_status(lbm_handle* h) { return check_status(h); }
+lbm_status lbm_internal_ensure_layout(lbm_handle* h) { return ensure_layout(h); }
 
 lbm_status lbm_internal_step(lbm_handle* h, cudaStream_t s) {
     return h->fp64() ? launch_one_step(h, h->kd, s) : launch_one_step(h, h->kf, s);
@@ -1071,6 +1092,7 @@ extern "C" lbm_status lbm_get_info(const lbm_handle* h, lbm_info* info) {
     info->ddf[0] = h->aa() ? h->f[0] : h->f[h->cur];
     info->ddf[1] = h->aa() ? nullptr : h->f[1 - h->cur];
     info->layout = h->chunked ? LBM_LAYOUT_CHUNKED : LBM_LAYOUT_SOA;
+    info->scheme = h->p.scheme;
     return LBM_OK;
 }
 
@@ -1091,6 +1113,25 @@ extern "C" lbm_status lbm_autotune(lbm_handle* h, int trial_steps, int* bx_out, 
         if (h->cuda(cudaEventSynchronize(ev[1]), "event sync")) return LBM_ERR_CUDA;
         return h->cuda(cudaEventElapsedTime(ms, ev[0], ev[1]), "event time");
     };
+    // 0. lattices created with LBM_STREAM_AUTO: A-B against in-place A-A
+    //    (with the default variant), where the switch is allowed
+    if (h->scheme_auto && !(h->t & 1) && !h->has_open_boundaries) {
+        const int s0 = h->p.scheme, s1 = s0 == LBM_STREAM_AB ? LBM_STREAM_AA : LBM_STREAM_AB;
+        float m0 = 0.f, m1 = 1e30f;
+        if ((st = trial(&m0)) != LBM_OK) { cudaEventDestroy(ev[0]); cudaEventDestroy(ev[1]); return st; }
+        if (trial_steps & 1) lbm_step(h, 1);   // back to an even step count
+        if (lbm_set_scheme(h, s1) == LBM_OK) {
+            if ((st = trial(&m1)) != LBM_OK) { cudaEventDestroy(ev[0]); cudaEventDestroy(ev[1]); return st; }
+            if (trial_steps & 1) lbm_step(h, 1);
+            if (m0 <= m1 && (st = lbm_set_scheme(h, s0)) != LBM_OK) {
+                cudaEventDestroy(ev[0]);
+                cudaEventDestroy(ev[1]);
+                return st;
+            }
+        } else {
+            h->err.clear();   // no memory for the second copy: stay
+        }
+    }
     // 1. the kernel variant, and with it the layout: GENERIC on the structure
     //    of arrays, PAIRED (chunked layout where nx is a multiple of 64),
     //    STAGED; those that do not apply to this lattice are skipped
@@ -1158,7 +1199,7 @@ extern "C" lbm_status lbm_set_scheme(lbm_handle* h, int scheme) {
     if (h->t & 1) return h->fail(LBM_ERR_STATE, "the streaming scheme can change after an even number of steps only");
     if (scheme == LBM_STREAM_AA && h->has_open_boundaries)
         return h->fail(LBM_ERR_UNSUPPORTED, "A-A streaming supports no OUTFLOW or FREESLIP cells");
-    const size_t fbytes = (size_t)h->q * h->N * h->sb;
+    const size_t fbytes = h->fbytes();
     if (scheme == LBM_STREAM_AB) {   // a second copy first: failing leaves the lattice as it was
         void* other = h->alloc(fbytes);
         if (!other) return h->fail(LBM_ERR_OOM, "second population copy");

@@ -34,6 +34,7 @@ struct lbm_ensemble {
     int total_tiles = 0;
     int tile = 256;                 // cells per tile (per-cell kernel: = threads per block)
     int variant = LBM_ENS_PER_CELL; // LBM_ENS_PER_CELL or LBM_ENS_PAIRED
+    int layout = LBM_LAYOUT_SOA;    // the members' layout: LBM_LAYOUT_SOA or LBM_LAYOUT_CHUNKED
     int warps = 4;                  // paired kernel: warps (runs of 64 cells) per tile
     std::vector<uint32_t> open;     // per member: a face holds non-solid cells
     bool idx32 = true;              // every member's q*N < 2^32
@@ -172,15 +173,20 @@ lbm_status launch(lbm_ensemble* e, int64_t s, cudaStream_t stream) {
     const int64_t t = e->t0[0] + s;
     const int scheme = !e->aa ? SCHEME_AB : ((t & 1) ? SCHEME_AA_LOC : SCHEME_AA_PP);
     const int parity = e->aa ? 0 : (int)(s & 1);
-    lbm_status st = e->variant == LBM_ENS_PAIRED
-                        ? e->cuda(e->ks->ens_pair(e->table, e->tile_member, parity, L), "paired ensemble kernel")
-                        : e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L),
-                                  "ensemble kernel");
+    const bool ch = e->layout == LBM_LAYOUT_CHUNKED;
+    lbm_status st;
+    if (e->variant == LBM_ENS_PAIRED)
+        st = e->cuda(e->ks->ens_pair[ch ? 1 : 0](e->table, e->tile_member, parity, L), "paired ensemble kernel");
+    else if (ch)
+        st = e->cuda(e->ks->ens_ch[scheme](e->table, e->tile_member, parity, L), "ensemble kernel");
+    else
+        st = e->cuda(e->ks->ens[scheme][e->idx32 ? 1 : 0](e->table, e->tile_member, parity, L), "ensemble kernel");
     if (st != LBM_OK || e->n_list == 0) return st;
     Launch B;
     B.block = dim3(256, 1, 1);
     B.grid = dim3((e->n_list + 255) / 256, 1, 1);
     B.stream = stream;
+    if (ch) return e->cuda(e->ks->ens_list_ch[scheme](e->table, e->list, e->n_list, parity, B), "ensemble list kernel");
     return e->cuda(e->ks->ens_list[scheme][e->idx32 ? 1 : 0](e->table, e->list, e->n_list, parity, B),
                    "ensemble list kernel");
 }
@@ -277,6 +283,13 @@ extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count,
 
 extern "C" lbm_status lbm_ensemble_destroy(lbm_ensemble* e) {
     if (!e) return LBM_OK;
+    // members on the chunked layout go back to the layout of their own settings
+    if (e->layout == LBM_LAYOUT_CHUNKED)
+        for (lbm_handle* h : e->m)
+            if (h->force_chunked && !h->sticky) {
+                h->force_chunked = false;
+                lbm_internal_ensure_layout(h);
+            }
     cudaStreamSynchronize(e->stream);
     e->drop_graphs();
     if (e->table) cudaFree(e->table);
@@ -341,8 +354,32 @@ extern "C" lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by) {
 }
 
 namespace {
-bool pair_ok(const lbm_ensemble* e) { return e->ks->ens_pair && !e->aa && e->idx32; }
+bool pair_ok(const lbm_ensemble* e) { return e->ks->ens_pair[0] && !e->aa && e->idx32; }
+bool chunked_ok(const lbm_ensemble* e) { return e->ks->ens_ch[0] && e->idx32; }
 }  // namespace
+
+extern "C" lbm_status lbm_ensemble_set_layout(lbm_ensemble* e, int layout) {
+    if (!e || (layout != LBM_LAYOUT_SOA && layout != LBM_LAYOUT_CHUNKED)) return LBM_ERR_ARG;
+    lbm_status st = check_members(e);
+    if (st != LBM_OK) return st;
+    if (layout == LBM_LAYOUT_CHUNKED && !chunked_ok(e)) {
+        e->err = "the chunked member layout needs 16-bit storage with FP32 arithmetic, SRT or TRT collision and "
+                 "q N < 2^32 for every member";
+        return LBM_ERR_UNSUPPORTED;
+    }
+    if (layout == e->layout) return LBM_OK;
+    for (lbm_handle* h : e->m) {
+        h->force_chunked = layout == LBM_LAYOUT_CHUNKED;
+        if ((st = lbm_internal_ensure_layout(h)) != LBM_OK) {
+            e->err = std::string("layout change: ") + lbm_last_error(h);
+            return st;
+        }
+    }
+    e->layout = layout;
+    return upload_table(e);
+}
+
+extern "C" int lbm_ensemble_get_layout(const lbm_ensemble* e) { return e ? e->layout : -1; }
 
 extern "C" lbm_status lbm_ensemble_set_variant(lbm_ensemble* e, int variant, int warps) {
     if (!e) return LBM_ERR_ARG;
@@ -438,30 +475,48 @@ extern "C" lbm_status lbm_ensemble_autotune(lbm_ensemble* e, int trial_steps, in
     lbm_status st = check_members(e);
     if (st != LBM_OK) return st;
     trial_steps += trial_steps & 1;       // whole A-A step pairs: the scheme may change between trials
-    float ms0 = 0.f, ms1 = INFINITY;
-    EnsConfig c0{LBM_ENS_PER_CELL, e->tile}, c1 = c0;
-    st = time_configs(e, trial_steps, &ms0, &c0);
-    if (st != LBM_OK) return st;
+    struct Best {
+        float ms = INFINITY;
+        int layout = LBM_LAYOUT_SOA, scheme = LBM_STREAM_AB;
+        EnsConfig c{LBM_ENS_PER_CELL, 256};
+    } best;
     const int scheme0 = e->aa ? LBM_STREAM_AA : LBM_STREAM_AB;
     const int scheme1 = e->aa ? LBM_STREAM_AB : LBM_STREAM_AA;
     // the other streaming scheme, where every member allows it (A-A: no
     // outflow or free-slip cells) and the memory for A-B copies is there
-    bool other = (scheme1 == LBM_STREAM_AB || can_use_aa(e)) && ((e->t0[0] + e->s) & 1) == 0;
-    if (other && (st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) == LBM_OK && switch_scheme(e, scheme1) == LBM_OK) {
-        st = time_configs(e, trial_steps, &ms1, &c1);
-        if (st != LBM_OK) return st;
-        if (ms0 <= ms1) {
-            if ((st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) != LBM_OK) return st;
-            if ((st = switch_scheme(e, scheme0)) != LBM_OK) return st;
+    const bool other = (scheme1 == LBM_STREAM_AB || can_use_aa(e)) && ((e->t0[0] + e->s) & 1) == 0;
+    std::vector<int> layouts{e->layout};
+    if (chunked_ok(e)) layouts.push_back(e->layout == LBM_LAYOUT_SOA ? LBM_LAYOUT_CHUNKED : LBM_LAYOUT_SOA);
+    for (int layout : layouts) {
+        if ((st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) != LBM_OK) return st;
+        if ((st = lbm_ensemble_set_layout(e, layout)) != LBM_OK) return st;
+        for (int pass = 0; pass < (other ? 2 : 1); ++pass) {
+            const int scheme = pass == 0 ? scheme0 : scheme1;
+            if (pass == 1) {
+                if ((st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) != LBM_OK) return st;
+                if (switch_scheme(e, scheme1) != LBM_OK) break;   // e.g. no memory for A-B copies
+            }
+            float ms = INFINITY;
+            EnsConfig c{LBM_ENS_PER_CELL, e->tile};
+            if ((st = time_configs(e, trial_steps, &ms, &c)) != LBM_OK) return st;
+            if (ms < best.ms) {
+                best.ms = ms;
+                best.layout = layout;
+                best.scheme = scheme;
+                best.c = c;
+            }
+            if (pass == 1) {
+                if ((st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) != LBM_OK) return st;
+                if ((st = switch_scheme(e, scheme0)) != LBM_OK) return st;
+            }
         }
-    } else {
-        if (st != LBM_OK) return st;
-        other = false;
     }
-    const EnsConfig best = other && ms1 < ms0 ? c1 : c0;
-    st = apply_config(e, best);
-    if (bx_out) *bx_out = best.variant == LBM_ENS_PAIRED ? 64 * best.size : best.size;
-    if (by_out) *by_out = best.variant == LBM_ENS_PAIRED ? best.size : 1;
+    if ((st = lbm_ensemble_set_variant(e, LBM_ENS_PER_CELL, 0)) != LBM_OK) return st;
+    if ((st = lbm_ensemble_set_layout(e, best.layout)) != LBM_OK) return st;
+    if (best.scheme != scheme0 && (st = switch_scheme(e, best.scheme)) != LBM_OK) return st;
+    st = apply_config(e, best.c);
+    if (bx_out) *bx_out = best.c.variant == LBM_ENS_PAIRED ? 64 * best.c.size : best.c.size;
+    if (by_out) *by_out = best.c.variant == LBM_ENS_PAIRED ? best.c.size : 1;
     return st;
 }
 

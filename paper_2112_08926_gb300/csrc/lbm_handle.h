@@ -40,7 +40,9 @@ struct lbm_handle {
     double check_tol = 0.0, check_mass0 = 0.0;
     int bx = 128, by = 2;
     int variant = 0;           // requested stream-collide kernel variant (LBM_VARIANT_*)
-    int chunked = 0;           // populations in the chunked layout (flag-free A-B, 16-bit)
+    bool scheme_auto = false;  // created with LBM_STREAM_AUTO: lbm_autotune also picks the scheme
+    int chunked = 0;           // populations in the chunked layout (16-bit storage, FP32 arithmetic)
+    bool force_chunked = false;   // chunked whatever nx (set by an ensemble that steps its members so)
     int num_sms = 0;
     int* status = nullptr;     // device status word written by bounded waits
     lbm_status sticky = LBM_OK;
@@ -61,6 +63,9 @@ struct lbm_handle {
     uint64_t graph_gen[2][2] = {{0, 0}, {0, 0}};
 
     bool aa() const { return p.scheme == LBM_STREAM_AA; }
+    // bytes of one population copy: 16-bit copies are padded to whole chunks
+    // of 64 cells, so that the chunked layout fits any cell count
+    size_t fbytes() const { return (size_t)q * (sb == 2 ? ((N + 63) & ~size_t(63)) : N) * sb; }
     // every population element index fits in 32 bits
     bool idx32() const { return (unsigned long long)q * N < (1ull << 32); }
     bool fp64() const { return p.arith == LBM_ARITH_FP64; }
@@ -130,6 +135,9 @@ lbm_status lbm_internal_step(lbm_handle* h, cudaStream_t s);
 // reads the device status word of h (after a stream synchronisation):
 // LBM_ERR_TIMEOUT, and the handle poisoned, if a bounded wait gave up
 lbm_status lbm_internal_check_status(lbm_handle* h);
+// brings the stored populations into the layout the settings of h call for
+// (after force_chunked changed)
+lbm_status lbm_internal_ensure_layout(lbm_handle* h);
 // device address of lbm_get_rho_u_static's staging array on the current
 // device, looked up once per device; NULL if the look-up failed (the CUDA
 // error is cleared)

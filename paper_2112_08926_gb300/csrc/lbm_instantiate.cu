@@ -23,9 +23,9 @@ namespace {
 using Real = std::conditional_t<LBM_ARITH == 1, double, float>;
 constexpr int FMT = LBM_FMT;
 
-template <class V, int COLL, int SCHEME, bool FLAGS, class IX>
+template <class V, int COLL, int SCHEME, bool FLAGS, class IX, bool CH = false>
 cudaError_t launch_step(const void* args, const Launch& L) {
-    k_step<V, COLL, FMT, Real, SCHEME, FLAGS, IX><<<L.grid, L.block, 0, L.stream>>>(
+    k_step<V, COLL, FMT, Real, SCHEME, FLAGS, IX, CH><<<L.grid, L.block, 0, L.stream>>>(
         *static_cast<const StepArgs<Real>*>(args));
     return cudaGetLastError();
 }
@@ -37,23 +37,23 @@ cudaError_t launch_list(const void* args, const uint32_t* cells, uint32_t count,
     return cudaGetLastError();
 }
 
-template <class V, int COLL, int SCHEME, class IX>
+template <class V, int COLL, int SCHEME, class IX, bool CH = false>
 cudaError_t launch_ens(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
-    k_ensemble_step<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
+    k_ensemble_step<V, COLL, FMT, Real, SCHEME, IX, CH><<<L.grid, L.block, 0, L.stream>>>(
         static_cast<const EnsMember<Real>*>(members), tile_member, parity);
     return cudaGetLastError();
 }
 
-template <class V, int COLL>
+template <class V, int COLL, bool CH>
 cudaError_t launch_ens_pair(const void* members, const uint32_t* tile_member, int parity, const Launch& L) {
-    k_ensemble_pair<V, COLL, FMT><<<L.grid, L.block, 0, L.stream>>>(
+    k_ensemble_pair<V, COLL, FMT, CH><<<L.grid, L.block, 0, L.stream>>>(
         static_cast<const EnsMember<float>*>(members), tile_member, parity);
     return cudaGetLastError();
 }
 
-template <class V, int COLL, int SCHEME, class IX>
+template <class V, int COLL, int SCHEME, class IX, bool CH = false>
 cudaError_t launch_ens_list(const void* members, const uint64_t* cells, uint32_t count, int parity, const Launch& L) {
-    k_ensemble_list<V, COLL, FMT, Real, SCHEME, IX><<<L.grid, L.block, 0, L.stream>>>(
+    k_ensemble_list<V, COLL, FMT, Real, SCHEME, IX, CH><<<L.grid, L.block, 0, L.stream>>>(
         static_cast<const EnsMember<Real>*>(members), cells, count, parity);
     return cudaGetLastError();
 }
@@ -140,8 +140,21 @@ void fill() {
             s.list_chunked[PH.value] = launch_list<V, COLL, PH.value, uint32_t, true>;
         });
     }
-    if constexpr (LBM_ARITH == 0 && (FMT == 2 || FMT == 3) && COLL < 2 && std::is_same<V, D3Q19>::value)
-        s.ens_pair = launch_ens_pair<V, COLL>;
+    // ensembles (D3Q19) of 16-bit members on the chunked layout, whatever
+    // their nx: per-cell and generic single-lattice kernels with chunked
+    // addressing; the paired ensemble kernel on both layouts (hardware
+    // conversions only)
+    if constexpr (LBM_ARITH == 0 && FMT >= 2 && COLL < 2 && std::is_same<V, D3Q19>::value) {
+        static_for<0, 3>([&](auto SC) {
+            s.step_ch[SC.value] = launch_step<V, COLL, SC.value, true, uint32_t, true>;
+            s.ens_ch[SC.value] = launch_ens<V, COLL, SC.value, uint32_t, true>;
+            s.ens_list_ch[SC.value] = launch_ens_list<V, COLL, SC.value, uint32_t, true>;
+        });
+        if constexpr (FMT == 2 || FMT == 3) {
+            s.ens_pair[0] = launch_ens_pair<V, COLL, false>;
+            s.ens_pair[1] = launch_ens_pair<V, COLL, true>;
+        }
+    }
     if constexpr (LBM_ARITH == 0 && FMT != 0 && COLL < 2 && std::is_same<V, D3Q19>::value) {
         s.staged[0] = launch_staged<V, COLL, 128>;
         s.staged[1] = launch_staged<V, COLL, 256>;

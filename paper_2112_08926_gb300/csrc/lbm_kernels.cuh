@@ -283,14 +283,16 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
 // instead of 4 keep them without spills.
 // FLAGS: the lattice has flags; then this kernel updates the plain cells
 // (flag byte 0) only and k_step_list the listed others.
-template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX>
+// CH: populations on the chunked layout (any nx; used for the members of an
+// ensemble that steps them on that layout).
+template <class V, int COLL, int FMT, class R, int SCHEME, bool FLAGS, class IX, bool CH = false>
 __global__ void __launch_bounds__(256, (sizeof(R) == 8 || (SCHEME == SCHEME_AA_PP && sizeof(IX) == 8)) ? 2 : (COLL == 2 ? 3 : 4))
     k_step(const StepArgs<R> a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.nx || y >= a.ny) return;
     // with flags: the flag-free update of the plain cells only (no boundary code)
-    cell_step<V, COLL, FMT, R, SCHEME, false, IX, FLAGS>(a, x, y, (int)blockIdx.z);
+    cell_step<V, COLL, FMT, R, SCHEME, false, IX, FLAGS, CH>(a, x, y, (int)blockIdx.z);
 }
 
 // The non-plain cells of a flagged lattice (solid cells excluded): boundary
@@ -802,8 +804,8 @@ __device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restri
 }
 
 // The plain cells (flag byte 0) of every member; the others come from the
-// ensemble's list (k_ensemble_list).
-template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
+// ensemble's list (k_ensemble_list).  CH: members on the chunked layout.
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX, bool CH = false>
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : (COLL == 2 ? 3 : 4)) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : (COLL == 2 ? 3 : 4))
     const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
     const uint32_t y = M.by_nx.div(r);
     const uint32_t x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, false, IX, true>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, false, IX, true, CH>(a, (int)x, (int)y, (int)z);
 }
 
 // Paired ensemble step, A-B, 16-bit storage with hardware conversion (FP16,
@@ -835,12 +837,20 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : (COLL == 2 ? 3 : 4))
 // (clamped) and write nothing.
 // the per-cell update of a cell on a lattice face (wrapped neighbours), kept
 // out of line so that the paired kernel's registers serve its common path
-template <class V, int COLL, int FMT>
+template <class V, int COLL, int FMT, bool CH>
 __device__ __noinline__ void ensemble_face_cell(const StepArgs<float>& a, int x, int y, int z) {
-    cell_step<V, COLL, FMT, float, SCHEME_AB, false, uint32_t, true>(a, x, y, z);
+    cell_step<V, COLL, FMT, float, SCHEME_AB, false, uint32_t, true, CH>(a, x, y, z);
 }
 
-template <class V, int COLL, int FMT>
+// element of slot i of cell m: structure of arrays (i N + m), or chunked
+// (chunk m / 64 holds its q slots of 64 codes: ((m/64) q + i) 64 + m % 64)
+template <class V, bool CH>
+__device__ __forceinline__ uint32_t ens_elem(int i, uint32_t m, uint32_t N) {
+    if constexpr (CH) return m + (m >> 6) * (uint32_t)((V::Q - 1) * CHUNK) + (uint32_t)(i * CHUNK);
+    else return (uint32_t)i * N + m;
+}
+
+template <class V, int COLL, int FMT, bool CH>
 __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>* __restrict__ members,
                                                           const uint32_t* __restrict__ tile_member, int parity) {
     using PC = PairCodec<FMT>;
@@ -860,7 +870,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
             const uint32_t fr = (ft - F.tile0) * blockDim.y + threadIdx.y;
             if (fr * 64u < F.ncells) {
                 const uint16_t* fs = (const uint16_t*)F.args[parity].src;
-                if (lane < V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(fs + (size_t)lane * F.ncells + fr * 64u));
+                if (lane < V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(fs + ens_elem<V, CH>(lane, fr * 64u, F.ncells)));
                 else if (lane == V::Q) asm volatile("prefetch.global.L2 [%0];" ::"l"(F.args[parity].flags + fr * 64u));
             }
         }
@@ -880,7 +890,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
             const uint32_t z = M.by_plane.div(c), r = c - z * plane, y = M.by_nx.div(r), x = r - y * (uint32_t)a.nx;
             if (x == 0u || x + 1u == (uint32_t)a.nx || y == 0u || y + 1u == (uint32_t)a.ny || z == 0u ||
                 z + 1u == (uint32_t)a.nz) {
-                ensemble_face_cell<V, COLL, FMT>(a, (int)x, (int)y, (int)z);
+                ensemble_face_cell<V, COLL, FMT, CH>(a, (int)x, (int)y, (int)z);
                 pl &= ~(1u << h);
                 bb &= ~(1u << h);
             }
@@ -889,19 +899,26 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
     if (!__any_sync(0xffffffffu, (pl | bb) != 0u)) return;
     const uint16_t* src = (const uint16_t*)a.src;
     uint16_t* dst = (uint16_t*)a.dst;
-    const uint32_t qN2 = (uint32_t)V::Q * N - 2u;                 // last even element start
+    // last even element start of the copy (chunked: padded to whole chunks)
+    const uint32_t qN2 = (uint32_t)V::Q * (CH ? ((N + 63u) & ~63u) : N) - 2u;
     uint32_t g[V::Q];
     static_for<0, V::Q>([&](auto I) {
         constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
         const int32_t d = cx + cy * a.nx + cz * (int32_t)plane;
-        const uint32_t e = (uint32_t)i * N + n - (uint32_t)d;     // element of the first cell's source
+        const uint32_t m = n - (uint32_t)d;                       // the first cell's source cell
+        // the aligned word holding element e of the source; lanes whose cells
+        // are not updated here may compute an element outside the copy, which
+        // the clamp brings back in (their codes are not used)
+        const uint32_t e = ens_elem<V, CH>(i, m, N);
         const uint32_t es = min(e & ~1u, qN2);
         const uint32_t w = *reinterpret_cast<const uint32_t*>(src + es);
-        if ((((uint32_t)i * N - (uint32_t)d) & 1u) == 0u) {        // warp-uniform
+        // the parity of e is the same in every lane (warp-uniform branch)
+        const bool odd = CH ? ((uint32_t)d & 1u) : ((((uint32_t)i * N - (uint32_t)d) & 1u) != 0u);
+        if (!odd) {
             g[i] = w;
         } else {                                                    // codes e, e + 1: hi of w, lo of the next word
             uint32_t nxt = __shfl_down_sync(0xffffffffu, w, 1);
-            if (lane == 31) nxt = (uint32_t)src[min(es + 2u, qN2 + 1u)];
+            if (lane == 31) nxt = (uint32_t)src[min(ens_elem<V, CH>(i, m + 1u, N), qN2 + 1u)];
             g[i] = __byte_perm(w, nxt, 0x5432);
         }
     });
@@ -918,7 +935,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
             static_for<1, V::Q>([&](auto I) {
                 constexpr int i = I.value;
                 if ((walls >> i) & 1u) {
-                    const uint32_t cc = src[(uint32_t)opposite(i) * N + c];
+                    const uint32_t cc = src[ens_elem<V, CH>(opposite(i), c, N)];
                     g[i] = h ? ((g[i] & 0xFFFFu) | (cc << 16)) : ((g[i] & 0xFFFF0000u) | cc);
                 }
             });
@@ -930,14 +947,15 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
         fa[I.value] = v.x;
         fb[I.value] = v.y;
     });
-    collide_pair<V, COLL, float, SL>(a.k, fa, fb);
+    const Relax<float> k = a.k;                                   // the member's constants in registers
+    collide_pair<V, COLL, float, SL>(k, fa, fb);
     const uint32_t ok = pl | bb;
     const uint32_t ok_up = __shfl_up_sync(0xffffffffu, ok, 1);
     static_for<0, V::Q>([&](auto I) {
         constexpr int i = I.value;
         const uint32_t own = PC::enc(fa[i], fb[i]);
-        const uint32_t e = (uint32_t)i * N + n;
-        if ((((uint32_t)i * N) & 1u) == 0u) {                      // warp-uniform: aligned pair
+        const uint32_t e = ens_elem<V, CH>(i, n, N);
+        if (CH || (((uint32_t)i * N) & 1u) == 0u) {                // warp-uniform: aligned pair
             if (ok == 3u) *reinterpret_cast<uint32_t*>(dst + e) = own;
             else if (ok == 1u) dst[e] = (uint16_t)own;
             else if (ok == 2u) dst[e + 1u] = (uint16_t)(own >> 16);
@@ -954,7 +972,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
 }
 
 // The non-plain cells of all members: entry = member << 32 | cell.
-template <class V, int COLL, int FMT, class R, int SCHEME, class IX>
+template <class V, int COLL, int FMT, class R, int SCHEME, class IX, bool CH = false>
 __global__ void __launch_bounds__(256) k_ensemble_list(const EnsMember<R>* __restrict__ members,
                                                         const uint64_t* __restrict__ cells, uint32_t count,
                                                         int parity) {
@@ -968,7 +986,7 @@ __global__ void __launch_bounds__(256) k_ensemble_list(const EnsMember<R>* __res
     const uint32_t r = n - z * (uint32_t)(a.nx * a.ny);
     const uint32_t y = M.by_nx.div(r);
     const uint32_t x = r - y * (uint32_t)a.nx;
-    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, false, false>(a, (int)x, (int)y, (int)z);
+    cell_step<V, COLL, FMT, R, SCHEME, true, IX, false, CH, false>(a, (int)x, (int)y, (int)z);
 }
 
 // ---------------------------------------------------------------- probes

@@ -27,9 +27,12 @@ struct KernelSet {
     StepFn step[3][2][2] = {};   // [scheme: AB, AA_PP, AA_LOC][flags][32-bit indices]
     ListFn list[3][2] = {};      // [scheme][32-bit indices]: the non-plain cells of a flagged lattice
     ListFn list_chunked[3] = {}; // [scheme]: the same on the chunked layout
+    StepFn step_ch[3] = {};      // [scheme]: generic kernel, chunked addressing, flags, 32-bit indices (D3Q19)
     EnsFn ens[3][2] = {};        // [scheme][32-bit indices], flags always on: plain cells
     EnsListFn ens_list[3][2] = {};   // the listed non-plain cells of all members
-    EnsFn ens_pair = nullptr;    // paired ensemble step (A-B, 32-bit indices, FP16 / FP16S, D3Q19)
+    EnsFn ens_pair[2] = {};      // paired ensemble step [chunked layout] (A-B, 32-bit indices, FP16 / FP16S, D3Q19)
+    EnsFn ens_ch[3] = {};        // [scheme]: per-cell ensemble step on the chunked layout (32-bit indices)
+    EnsListFn ens_list_ch[3] = {};   // [scheme]: the listed cells on the chunked layout
     ProbeFn probe[8] = {};    // [layout code: phase | 4 if chunked]
     PutFn put[4] = {};        // [bit 0: A-A, bit 1: chunked]
     StagedFn staged[3] = {};  // row length 128, 256, 512 (D3Q19, FP32 arithmetic only)

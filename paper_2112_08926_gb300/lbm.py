@@ -29,7 +29,7 @@ COLLISIONS = {"SRT": 0, "TRT": 1, "MRT": 2}
 STORAGES = {"FP64": 0, "FP32": 1, "FP16": 2, "FP16S": 3, "FP16C": 4,
             "P16_0S": 5, "P16_1S": 6, "P16_2C": 7, "P16_0": 8, "P16_1": 9}
 ARITHS = {"FP32": 0, "FP64": 1}
-SCHEMES = {"AB": 0, "AA": 1}
+SCHEMES = {"AB": 0, "AA": 1, "AUTO": 2}
 VARIANTS = {"auto": 0, "generic": 1, "staged": 2, "paired": 3}
 Q = {"D2Q9": 9, "D3Q19": 19, "D3Q27": 27}
 WALL, MOVING, EQ, OUTFLOW, FREESLIP = 0x01, 0x02, 0x04, 0x08, 0x10
@@ -43,7 +43,7 @@ EXPORTS = [
     "lbm_ensemble_last_error", "lbm_set_variant", "lbm_get_variant", "lbm_get_rho_u_static",
     "lbm_set_nodes", "lbm_get_f_cells", "lbm_get_rho_u_cells", "lbm_selftest_wait_timeout",
     "lbm_set_scheme", "lbm_ensemble_scheme", "lbm_set_divergence_check", "lbm_codec_encode_bits_table",
-    "lbm_ensemble_set_variant", "lbm_ensemble_get_variant",
+    "lbm_ensemble_set_variant", "lbm_ensemble_get_variant", "lbm_ensemble_set_layout", "lbm_ensemble_get_layout",
 ]
 
 
@@ -76,6 +76,7 @@ class lbm_info(ctypes.Structure):
         ("q", ctypes.c_int), ("cells", ctypes.c_int64), ("step", ctypes.c_int64),
         ("bytes_per_population", ctypes.c_int), ("has_flags", ctypes.c_int),
         ("device_bytes", ctypes.c_size_t), ("ddf", ctypes.c_void_p * 2), ("layout", ctypes.c_int),
+        ("scheme", ctypes.c_int),
     ]
 
 
@@ -128,6 +129,8 @@ def load() -> ctypes.CDLL:
             "lbm_ensemble_set_block": [P, I, I],
             "lbm_ensemble_set_variant": [P, I, I],
             "lbm_ensemble_get_variant": [P],
+            "lbm_ensemble_set_layout": [P, I],
+            "lbm_ensemble_get_layout": [P],
             "lbm_ensemble_autotune": [P, I, pI, pI],
             "lbm_ensemble_destroy": [P],
             "lbm_set_variant": [P, I],
@@ -242,7 +245,8 @@ class Lattice:
         self.shape = (nz, ny, nx)
         self.N = nx * ny * nz
         self.q = Q[velset]
-        self.velset, self.storage, self.scheme = velset, storage, scheme
+        self.velset, self.storage = velset, storage
+        self.scheme = {0: "AB", 1: "AA"}[self.info().scheme]   # AUTO resolved at creation
 
     def close(self):
         if self._h:
@@ -354,6 +358,7 @@ class Lattice:
         shape by timing (lbm_autotune); returns (bx, by)."""
         bx, by = ctypes.c_int(), ctypes.c_int()
         self._c(self._L.lbm_autotune(self._h, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)))
+        self.scheme = {0: "AB", 1: "AA"}[self.info().scheme]
         return bx.value, by.value
 
     def set_scheme(self, scheme: str):
@@ -408,6 +413,14 @@ class Ensemble:
 
     def variant(self) -> str:
         return {0: "per_cell", 1: "paired"}[self._L.lbm_ensemble_get_variant(self._e)]
+
+    def set_layout(self, layout):
+        """'soa' or 'chunked' (the members' population layout; see
+        lbm_ensemble_set_layout)."""
+        _check(self._L.lbm_ensemble_set_layout(self._e, {"soa": 0, "chunked": 1}[layout]), self._e, ensemble=True)
+
+    def layout(self) -> str:
+        return {0: "soa", 1: "chunked"}[self._L.lbm_ensemble_get_layout(self._e)]
 
     def autotune(self, trial_steps=5):
         """Picks kernel, tile and streaming scheme; returns (cells per tile,

@@ -47,7 +47,7 @@ def _params(P, **kw):
 @pytest.mark.parametrize("kw,status", [
     (dict(tau=0.5), 1), (dict(tau=float("nan")), 1), (dict(nx=0), 1), (dict(velset=3), 1),
     (dict(velset=0, nz=2), 1), (dict(collision=3), 1), (dict(collision=2, velset=0, nz=1), 4), (dict(storage=10), 1), (dict(arith=2), 1),
-    (dict(scheme=2), 1), (dict(collision=1, trt_lambda=0.0), 1),
+    (dict(scheme=3), 1), (dict(collision=1, trt_lambda=0.0), 1),
     (dict(arith=1, storage=3), 4),                       # FP64 arithmetic with 16-bit storage
     (dict(nx=1300, ny=1300, nz=1300), 4),                # more than 2^31 cells
 ])

@@ -331,7 +331,7 @@ def test_cylinder_poiseuille_umax_sweeps():
                 if storage in unshifted:
                     err_ns[(R, re, m, storage)] = cylinder_poiseuille_error(
                         P, arith, storage, R, u_max=u, re=re, shifting=False, block=(1, 32))
-            lines.append(f"R={R:2d} Re={re:5.1f} u_max={u:.3e} ({m:3.1f} u_tau1)  " + "  ".join(row))
+            lines.append(f"R={R:2d} Re={re:5.1f} u_max={u:.3e} ({m:4.2f} u_tau1)  " + "  ".join(row))
             lines.append("              unshifted                    " + "  ".join(
                 f"{err_ns[(R, re, m, s)]:.2e}" if s in unshifted else "   -    " for _, s in tiers))
     print("\nCylinder Poiseuille u_max sweeps, D3Q19 SRT: relative L2 error of u_x\n"

@@ -69,13 +69,42 @@ def test_paired_ensemble_equals_per_member_launches(storage, coll):
 
     a, b = members(), members()
     ea, eb = P.Ensemble(a), P.Ensemble(b)
-    for warps in (4, 1, 2):
+    for layout, warps in (("soa", 4), ("soa", 1), ("chunked", 2), ("chunked", 4)):
+        ea.set_layout(layout)
         ea.set_variant("paired", warps)
-        assert ea.variant() == "paired"
+        assert ea.variant() == "paired" and ea.layout() == layout
         ea.step(70)          # a graph replay of 64 steps and 6 single launches
         eb.step_each(70)
         for ga, gb in zip(a, b):
-            assert np.array_equal(ga.f(), gb.f()), warps
+            assert np.array_equal(ga.f(), gb.f()), (layout, warps)
+
+
+@pytest.mark.parametrize("scheme", ["AB", "AA"])
+def test_chunked_member_layout_every_kernel(scheme):
+    """Members on the chunked layout (64-cell chunks of the linear cell
+    index, any nx): the per-cell ensemble kernel, one launch per member on
+    the same layout (lbm_ensemble_step_each), and the members' readbacks,
+    against members on the structure of arrays."""
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=6, n_min=5, n_max=19, seed=3)
+    a = make_members(specs, "FP16C", scheme, P)
+    b = make_members(specs, "FP16C", scheme, P)
+    c = make_members(specs, "FP16C", scheme, P)
+    ea, eb, ec = P.Ensemble(a), P.Ensemble(b), P.Ensemble(c)
+    ea.set_layout("chunked")
+    eb.set_layout("chunked")
+    assert a[0].info().layout == 1
+    ea.step(70)
+    eb.step_each(70)
+    ec.step(70)
+    for ga, gb, gc in zip(a, b, c):
+        fa = ga.f()
+        assert np.array_equal(fa, gb.f()) and np.array_equal(fa, gc.f())
+        assert np.array_equal(ga.rho_u()[1], gc.rho_u()[1])
+    ea.close()
+    assert a[0].info().layout == 0       # back to the members' own layout
+    for ga, gc in zip(a, c):
+        assert np.array_equal(ga.f(), gc.f())
 
 
 def test_paired_ensemble_open_faces_and_every_cell_kind():
@@ -98,11 +127,13 @@ def test_paired_ensemble_open_faces_and_every_cell_kind():
 
     a, b = members(), members()
     ea, eb = P.Ensemble(a), P.Ensemble(b)
-    ea.set_variant("paired", 2)
-    ea.step(70)
-    eb.step_each(70)
-    for ga, gb in zip(a, b):
-        assert np.array_equal(ga.f(), gb.f())
+    for layout in ("soa", "chunked"):
+        ea.set_layout(layout)
+        ea.set_variant("paired", 2)
+        ea.step(70)
+        eb.step_each(70)
+        for ga, gb in zip(a, b):
+            assert np.array_equal(ga.f(), gb.f()), layout
 
 
 def test_paired_ensemble_members_match_oracle():
@@ -110,6 +141,7 @@ def test_paired_ensemble_members_match_oracle():
     specs = W.ensemble_cavities(count=3, n_min=5, n_max=12, seed=98)
     mem = make_members(specs, "FP16S", "AB", P)
     e = P.Ensemble(mem)
+    e.set_layout("chunked")
     e.set_variant("paired", 4)
     e.step(70)
     for s, g in zip(specs, mem):

@@ -632,3 +632,30 @@ def test_mrt_unsupported_combinations():
         with pytest.raises(P().LBMError) as e:
             P().Lattice(8, 4, nz, vs, "MRT", storage, arith, "AB")
         assert e.value.status == 4
+
+
+
+def test_stream_auto_picks_a_scheme_and_keeps_results():
+    """LBM_STREAM_AUTO: created as A-B where both copies fit; lbm_autotune
+    times A-B against in-place A-A and keeps the faster.  Every choice gives
+    the populations of a fixed-scheme run bit for bit (same step count)."""
+    import paper_2112_08926_gb300 as P
+    shape = (12, 10, 64)
+    nz, ny, nx = shape
+    fields = W.random_fields(shape, seed=31)
+    flags = W.cavity(nx, 0.05, ny=ny, nz=nz)
+    g = P.Lattice(nx, ny, nz, "D3Q19", "TRT", "FP16S", "FP32", "AUTO", tau=0.6)
+    assert g.scheme == "AB"
+    g.set_geometry(*flags)
+    g.set_rho_u(*fields)
+    g.autotune(trial_steps=7)
+    assert g.scheme in ("AB", "AA")
+    steps = g.info().step
+    g.step(10 + (steps & 1))
+    ref = P.Lattice(nx, ny, nz, "D3Q19", "TRT", "FP16S", "FP32", "AB", tau=0.6)
+    ref.set_geometry(*flags)
+    ref.set_rho_u(*fields)
+    ref.step(g.info().step)
+    assert np.array_equal(g.f(), ref.f())
+    g.close()
+    ref.close()
