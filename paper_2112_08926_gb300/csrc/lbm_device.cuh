@@ -541,8 +541,42 @@ __device__ __forceinline__ void moments(const R* g, R& rho, R* j, R sh) {
 
 // Velocity u_a = x_a / rho with x_a = j_a + F_a/2 (Sec. 2.2: each momentum
 // component divided by rho, u_x = (f1 - f2 + ...)/rho; Guo half-force), before
-// clamping: one IEEE division per component.  j is the scaled momentum; its
-// 2^-SL is exact.
+// clamping, as the IEEE quotient of each component.  It is computed from one
+// IEEE reciprocal y = 1/rho (rounded to nearest) by two FMA corrections:
+//   q0 = x y;  q1 = q0 + (x - rho q0) y;  u = q1 + (x - rho q1) y.
+// q0 can lie up to 1.5 ulp off x/rho; after the first correction q1 is within
+// one ulp (faithful), so x - rho q1 is exact, and by Markstein's theorem
+// (P. Markstein, IBM J. Res. Dev. 34 (1990) 111: a faithful quotient
+// corrected with the correctly rounded reciprocal) u is the correctly rounded
+// quotient -- provided nothing underflows or overflows, which holds for
+// |x| in [2^-80, 2^80] and rho in [2^-20, 2^20] (FP64: 2^-800, 2^800 and
+// 2^-200, 2^200).  A zero x gives +0; the sign of x is copied back.  Outside
+// those ranges the IEEE division itself is taken.  (Three IEEE divisions give
+// the same bits; on lattices at rest they ran much slower.)
+template <class R> struct DivRange;
+template <> struct DivRange<float> {
+    static constexpr float xlo = 0x1p-80f, xhi = 0x1p80f, rlo = 0x1p-20f, rhi = 0x1p20f;
+};
+template <> struct DivRange<double> {
+    static constexpr double xlo = 0x1p-800, xhi = 0x1p800, rlo = 0x1p-200, rhi = 0x1p200;
+};
+
+template <class R>
+__device__ __forceinline__ R div_corrected(R x, R rho, R y, bool& ok) {
+    const R ax = fabs(x);
+    ok = ok && (x == R(0) || (ax >= DivRange<R>::xlo && ax <= DivRange<R>::xhi));
+    const R q0 = x * y;
+    const R q1 = fmaR(fmaR(-q0, rho, x), y, q0);
+    return copysign(fmaR(fmaR(-q1, rho, x), y, q1), x);
+}
+
+template <class R>
+__device__ __forceinline__ bool rho_in_range(R rho) {
+    return rho >= DivRange<R>::rlo && rho <= DivRange<R>::rhi;
+}
+
+// the numerators x_a = j_a 2^-SL (+ F_a / 2); j is the scaled momentum and
+// its 2^-SL exact
 template <class R, int SL>
 __device__ __forceinline__ void numerators(const Relax<R>& k, const R* j, R* x) {
 #pragma unroll
@@ -556,21 +590,37 @@ template <class R, int SL>
 __device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
     R x[3];
     numerators<R, SL>(k, j, x);
+    const R y = R(1) / rho;
+    bool ok = rho_in_range(rho);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = x[a] / rho;
+    for (int a = 0; a < 3; ++a) u[a] = div_corrected(x[a], rho, y, ok);
+    if (!ok) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = x[a] / rho;
+    }
 }
 
-// the same for two cells, so that the six divisions overlap
+// the same for two cells, whose reciprocals and corrections overlap; one
+// fallback for both
 template <class R, int SL>
 __device__ __forceinline__ void velocity_pair(const Relax<R>& k, R ra, const R* ja, R* ua, R rb, const R* jb,
                                               R* ub) {
     R xa[3], xb[3];
     numerators<R, SL>(k, ja, xa);
     numerators<R, SL>(k, jb, xb);
+    const R ya = R(1) / ra, yb = R(1) / rb;
+    bool ok = rho_in_range(ra) && rho_in_range(rb);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        ua[a] = xa[a] / ra;
-        ub[a] = xb[a] / rb;
+        ua[a] = div_corrected(xa[a], ra, ya, ok);
+        ub[a] = div_corrected(xb[a], rb, yb, ok);
+    }
+    if (!ok) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            ua[a] = xa[a] / ra;
+            ub[a] = xb[a] / rb;
+        }
     }
 }
 

@@ -880,6 +880,9 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
     const uint32_t f1 = n + 1u < N ? (uint32_t)a.flags[n + 1u] : F_WALL;
     uint32_t pl = (f0 == 0u ? 1u : 0u) | (f1 == 0u ? 2u : 0u);             // updated here: plain ...
     uint32_t bb = (f0 == F_NEAR_SOLID ? 1u : 0u) | (f1 == F_NEAR_SOLID ? 2u : 0u);   // ... and bounce-back
+    // halves the stores leave alone: solid cells and cells past the member
+    // (their populations stay zero) and cells the per-cell path updated
+    uint32_t skip = ((f0 & F_WALL) ? 1u : 0u) | ((f1 & F_WALL) ? 2u : 0u);
     const uint32_t plane = (uint32_t)a.nx * (uint32_t)a.ny;
     if (M.open && ((pl | bb) != 0u)) {
         // cells on a face need wrapped neighbours: the per-cell path
@@ -893,6 +896,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
                 ensemble_face_cell<V, COLL, FMT, CH>(a, (int)x, (int)y, (int)z);
                 pl &= ~(1u << h);
                 bb &= ~(1u << h);
+                skip |= 1u << h;
             }
         }
     }
@@ -949,24 +953,31 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
     });
     const Relax<float> k = a.k;                                   // the member's constants in registers
     collide_pair<V, COLL, float, SL>(k, fa, fb);
-    const uint32_t ok = pl | bb;
-    const uint32_t ok_up = __shfl_up_sync(0xffffffffu, ok, 1);
+    // Every other half is written: the listed cells' halves carry values the
+    // list launch that follows overwrites, so the stores are whole words,
+    // the skipped halves masked to zero, except where a word would reach
+    // past the member (structure of arrays) or into a skipped cell the per-cell
+    // path wrote.
+    const uint32_t keep = ((skip & 1u) ? 0u : 0x0000FFFFu) | ((skip & 2u) ? 0u : 0xFFFF0000u);
+    const bool face_done = M.open != 0u && skip != (((f0 & F_WALL) ? 1u : 0u) | ((f1 & F_WALL) ? 2u : 0u));
+    const uint32_t w3 = (skip == 3u) ? 0u : (face_done || (!CH && n + 1u >= N) ? (skip ^ 3u) : 3u);
+    const uint32_t w3_up = __shfl_up_sync(0xffffffffu, w3, 1);
     static_for<0, V::Q>([&](auto I) {
         constexpr int i = I.value;
-        const uint32_t own = PC::enc(fa[i], fb[i]);
+        const uint32_t own = PC::enc(fa[i], fb[i]) & keep;
         const uint32_t e = ens_elem<V, CH>(i, n, N);
         if (CH || (((uint32_t)i * N) & 1u) == 0u) {                // warp-uniform: aligned pair
-            if (ok == 3u) *reinterpret_cast<uint32_t*>(dst + e) = own;
-            else if (ok == 1u) dst[e] = (uint16_t)own;
-            else if (ok == 2u) dst[e + 1u] = (uint16_t)(own >> 16);
+            if (w3 == 3u) *reinterpret_cast<uint32_t*>(dst + e) = own;
+            else if (w3 == 1u) dst[e] = (uint16_t)own;
+            else if (w3 == 2u) dst[e + 1u] = (uint16_t)(own >> 16);
         } else {                                                    // word e-1: previous lane's upper, own lower code
             const uint32_t up = __shfl_up_sync(0xffffffffu, own, 1);
-            const uint32_t okw = (lane == 0 ? 0u : ((ok_up >> 1) & 1u)) | ((ok & 1u) << 1);
+            const uint32_t okw = (lane == 0 ? 0u : ((w3_up >> 1) & 1u)) | ((w3 & 1u) << 1);
             const uint32_t w = __byte_perm(up, own, 0x5432);
             if (okw == 3u) *reinterpret_cast<uint32_t*>(dst + e - 1u) = w;
             else if (okw == 2u) dst[e] = (uint16_t)own;
             else if (okw == 1u) dst[e - 1u] = (uint16_t)(up >> 16);
-            if (lane == 31 && (ok & 2u)) dst[e + 1u] = (uint16_t)(own >> 16);   // cell n + 1: the next run's word
+            if (lane == 31 && (w3 & 2u)) dst[e + 1u] = (uint16_t)(own >> 16);   // cell n + 1: the next run's word
         }
     });
 }
