@@ -337,7 +337,11 @@ typedef struct lbm_ensemble lbm_ensemble;
  * scheme (LBM_ERR_ARG otherwise; other velocity sets LBM_ERR_UNSUPPORTED),
  * have flags set and the same step parity.  The members keep their own data;
  * the ensemble adds a device descriptor table and a per-tile member table.
- * All launches go to the first member's stream. */
+ * All launches go to the first member's stream; where members have other
+ * streams, each ensemble call first makes that stream wait (by events, the
+ * host does not block) for the work already queued on theirs, and a step
+ * makes their streams wait for its launches, so member calls before and
+ * after ensemble steps stay in order. */
 lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out);
 /* Advance every member nsteps steps: per step one launch over the plain
  * cells of all members and one over the listed boundary cells of all

@@ -315,6 +315,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
     ++h->gen;
+    ++h->geom_gen;
     const size_t N = h->N;
     if (!flags) {
         h->has_open_boundaries = false;
@@ -431,6 +432,7 @@ extern "C" lbm_status lbm_set_nodes(lbm_handle* h, int64_t count, const int64_t*
     lbm_status st = check_handle(h);
     if (st != LBM_OK) return st;
     ++h->gen;
+    ++h->geom_gen;
     if (!h->flags) return h->fail(LBM_ERR_ARG, "lbm_set_nodes needs flags (call lbm_set_geometry first)");
     if ((st = check_cell_list(h, count, cells)) != LBM_OK) return st;
     {

@@ -20,6 +20,30 @@ namespace {
 constexpr int kGraphSteps = 64;
 }
 
+// What the ensemble's tables took from a member: its copies, flags, node
+// arrays and cell list, layout and scheme.  A member changed outside the
+// ensemble (a new geometry, scheme or layout) no longer matches.
+struct MemberKey {
+    const void* f[2];
+    const void* flags;
+    const void* node_u;
+    const void* node_rho;
+    const void* special;
+    uint32_t n_complex;
+    int chunked, scheme;
+    uint64_t geom_gen;
+    explicit MemberKey(const lbm_handle* h = nullptr)
+        : f{h ? h->f[0] : nullptr, h ? h->f[1] : nullptr}, flags(h ? h->flags : nullptr),
+          node_u(h ? h->node_u : nullptr), node_rho(h ? h->node_rho : nullptr), special(h ? h->special : nullptr),
+          n_complex(h ? h->n_complex : 0u), chunked(h ? h->chunked : 0), scheme(h ? h->p.scheme : 0),
+          geom_gen(h ? h->geom_gen : 0u) {}
+    bool operator==(const MemberKey& o) const {
+        return f[0] == o.f[0] && f[1] == o.f[1] && flags == o.flags && node_u == o.node_u && node_rho == o.node_rho &&
+               special == o.special && n_complex == o.n_complex && chunked == o.chunked && scheme == o.scheme &&
+               geom_gen == o.geom_gen;
+    }
+};
+
 struct lbm_ensemble {
     std::vector<lbm_handle*> m;
     cudaStream_t stream = nullptr;
@@ -40,7 +64,10 @@ struct lbm_ensemble {
     bool idx32 = true;              // every member's q*N < 2^32
     int64_t s = 0;                  // steps taken through the ensemble
     std::vector<int64_t> t0;        // member step counters at creation
+    std::vector<MemberKey> keys;    // the members as the tables hold them
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    std::vector<cudaStream_t> member_streams;   // the members' own streams other than `stream`
+    cudaEvent_t order = nullptr;                // orders those streams against `stream`
     std::string err;
 
     lbm_status cuda(cudaError_t e, const char* what) {
@@ -55,6 +82,27 @@ struct lbm_ensemble {
 };
 
 namespace {
+
+// Members run their own calls (readbacks, layout and scheme changes) on their
+// own streams and the ensemble's launches go to `stream`: to_ensemble makes
+// `stream` wait for the work queued so far on the members' streams, the
+// reverse makes the members' streams wait for the ensemble's work.  Nothing
+// blocks the host.
+lbm_status order_streams(lbm_ensemble* e, bool to_ensemble) {
+    if (e->member_streams.empty()) return LBM_OK;
+    if (!e->order && e->cuda(cudaEventCreateWithFlags(&e->order, cudaEventDisableTiming), "event")) return LBM_ERR_CUDA;
+    if (to_ensemble) {
+        for (cudaStream_t s : e->member_streams)
+            if (e->cuda(cudaEventRecord(e->order, s), "event record") ||
+                e->cuda(cudaStreamWaitEvent(e->stream, e->order, 0), "stream wait"))
+                return LBM_ERR_CUDA;
+        return LBM_OK;
+    }
+    if (e->cuda(cudaEventRecord(e->order, e->stream), "event record")) return LBM_ERR_CUDA;
+    for (cudaStream_t s : e->member_streams)
+        if (e->cuda(cudaStreamWaitEvent(s, e->order, 0), "stream wait")) return LBM_ERR_CUDA;
+    return LBM_OK;
+}
 
 // sets *out if a cell on a face of the lattice is not solid
 __global__ void k_face_open(const uint8_t* __restrict__ flags, int nx, int ny, int nz, int* out) {
@@ -124,6 +172,7 @@ lbm_status upload_table(lbm_ensemble* e) {
     std::vector<EnsMember<double>> td;
     if (e->fp64) { td = make_table<double>(e, tiles); src = td.data(); bytes = td.size() * sizeof(EnsMember<double>); }
     else { tf = make_table<float>(e, tiles); src = tf.data(); bytes = tf.size() * sizeof(EnsMember<float>); }
+    if (order_streams(e, true) != LBM_OK) return LBM_ERR_CUDA;   // members' relayouts and scheme swaps first
     if (e->cuda(cudaStreamSynchronize(e->stream), "sync")) return LBM_ERR_CUDA;
     if (!e->table) {
         if (e->cuda(cudaMalloc(&e->table, bytes), "table alloc")) return LBM_ERR_OOM;
@@ -161,6 +210,8 @@ lbm_status upload_table(lbm_ensemble* e) {
     }
     if (e->cuda(cudaStreamSynchronize(e->stream), "sync")) return LBM_ERR_CUDA;
     e->drop_graphs();
+    e->keys.clear();
+    for (const lbm_handle* h : e->m) e->keys.emplace_back(h);
     return LBM_OK;
 }
 
@@ -196,6 +247,10 @@ lbm_status check_members(lbm_ensemble* e) {
         if (e->m[k]->sticky) return LBM_ERR_STATE;
         if (e->m[k]->t != e->t0[k] + e->s) {
             e->err = "a member was stepped or re-initialised outside the ensemble; create a new ensemble";
+            return LBM_ERR_STATE;
+        }
+        if (k < e->keys.size() && !(MemberKey(e->m[k]) == e->keys[k])) {
+            e->err = "a member's geometry, nodes, scheme or layout changed outside the ensemble; create a new ensemble";
             return LBM_ERR_STATE;
         }
     }
@@ -245,6 +300,13 @@ extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count,
     for (lbm_handle* h : e->m) {
         e->t0.push_back(h->t);
         e->idx32 = e->idx32 && h->idx32();
+        if (h->stream != e->stream &&
+            std::find(e->member_streams.begin(), e->member_streams.end(), h->stream) == e->member_streams.end())
+            e->member_streams.push_back(h->stream);
+    }
+    if (order_streams(e, true) != LBM_OK) {   // the members' geometry and fields are set
+        lbm_ensemble_destroy(e);
+        return LBM_ERR_CUDA;
     }
     if (cudaStreamCreateWithFlags(&e->capture, cudaStreamNonBlocking) != cudaSuccess) {
         delete e;
@@ -283,6 +345,8 @@ extern "C" lbm_status lbm_ensemble_create(lbm_handle* const* members, int count,
 
 extern "C" lbm_status lbm_ensemble_destroy(lbm_ensemble* e) {
     if (!e) return LBM_OK;
+    // the ensemble's launches end before the members' streams touch their copies
+    cudaStreamSynchronize(e->stream);
     // members on the chunked layout go back to the layout of their own settings
     if (e->layout == LBM_LAYOUT_CHUNKED)
         for (lbm_handle* h : e->m)
@@ -296,6 +360,7 @@ extern "C" lbm_status lbm_ensemble_destroy(lbm_ensemble* e) {
     if (e->tile_member) cudaFree(e->tile_member);
     if (e->list) cudaFree(e->list);
     if (e->capture) cudaStreamDestroy(e->capture);
+    if (e->order) cudaEventDestroy(e->order);
     delete e;
     return LBM_OK;
 }
@@ -304,6 +369,7 @@ extern "C" lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps) {
     if (!e || nsteps < 0) return LBM_ERR_ARG;
     lbm_status st = check_members(e);
     if (st != LBM_OK) return st;
+    if ((st = order_streams(e, true)) != LBM_OK) return st;
     int64_t done = 0;
     while (nsteps - done >= kGraphSteps) {
         const int key = (int)((e->aa ? e->t0[0] + e->s : e->s) & 1);
@@ -328,13 +394,14 @@ extern "C" lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps) {
         if (st != LBM_OK) return st;
         advance_members(e, 1);
     }
-    return LBM_OK;
+    return order_streams(e, false);
 }
 
 extern "C" lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps) {
     if (!e || nsteps < 0) return LBM_ERR_ARG;
     lbm_status st = check_members(e);
     if (st != LBM_OK) return st;
+    if ((st = order_streams(e, true)) != LBM_OK) return st;
     for (int64_t k = 0; k < nsteps; ++k) {
         for (lbm_handle* h : e->m) {
             st = lbm_internal_step(h, e->stream);   // advances h's counters
@@ -342,7 +409,7 @@ extern "C" lbm_status lbm_ensemble_step_each(lbm_ensemble* e, int64_t nsteps) {
         }
         e->s += 1;
     }
-    return LBM_OK;
+    return order_streams(e, false);
 }
 
 extern "C" lbm_status lbm_ensemble_set_block(lbm_ensemble* e, int bx, int by) {
@@ -454,6 +521,9 @@ lbm_status switch_scheme(lbm_ensemble* e, int scheme) {
         if (st != LBM_OK) {   // e.g. no memory for A-B copies: undo the members switched so far
             e->err = std::string("scheme switch: ") + lbm_last_error(e->m[k]);
             for (size_t j = 0; j < k; ++j) lbm_set_scheme(e->m[j], back);
+            // the members switched back hold new copies: tables from them
+            const std::string why = e->err;
+            if (upload_table(e) == LBM_OK) e->err = why;
             return st;
         }
     }

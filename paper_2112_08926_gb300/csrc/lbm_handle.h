@@ -58,6 +58,7 @@ struct lbm_handle {
     // is valid while `gen` (bumped by every call that changes what a step
     // launches) equals the value it was captured at
     uint64_t gen = 0;
+    uint64_t geom_gen = 0;     // bumped by lbm_set_geometry and lbm_set_nodes (cell lists, node values)
     cudaStream_t capture = nullptr;
     cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     uint64_t graph_gen[2][2] = {{0, 0}, {0, 0}};

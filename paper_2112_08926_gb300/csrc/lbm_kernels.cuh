@@ -774,10 +774,12 @@ template <class R> struct EnsMember {
 };
 
 // L2 prefetch for the tile a.pf tiles further in launch order (about one
-// wave later, since blocks start in launch order): its q population ranges
-// and its flag bytes, one 128-byte line per thread; the bytes read from HBM
-// stay the same.  16-bit formats with hardware conversion only (HBM-bound).
-template <class V, int FMT, class R>
+// wave later, since blocks start in launch order): its population codes and
+// its flag bytes, one 128-byte line per thread; the bytes read from HBM stay
+// the same.  Structure of arrays: q ranges of the tile's cells; chunked
+// (CH): the whole chunks that hold its cells, q lines each.  16-bit formats
+// with hardware conversion only (HBM-bound).
+template <class V, int FMT, bool CH, class R>
 __device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restrict__ members,
                                                     const uint32_t* __restrict__ tile_member, int parity, int pf) {
     if constexpr (FMT == 2 || FMT == 3) {
@@ -785,21 +787,29 @@ __device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restri
         constexpr uint32_t LINE = 128 / sizeof(T);
         const uint32_t ft = blockIdx.x + (uint32_t)pf;
         if (pf <= 0 || ft >= gridDim.x) return;
-        // lines per population range: one more than whole lines, for a range
-        // that does not start on a line boundary
-        const uint32_t per = (blockDim.x + LINE - 1) / LINE + 1;
         const uint32_t t = threadIdx.x;
-        if (t >= V::Q * per + 2) return;
         const EnsMember<R>& F = members[__ldg(tile_member + ft)];
         const uint32_t n0 = (ft - F.tile0) * blockDim.x;
         const uint32_t last = min(blockDim.x, F.ncells - n0) - 1;   // tile ft holds cells n0 .. n0 + last
-        if (t < V::Q * per) {
-            const uint32_t i = t / per, k = t - i * per;
-            const T* src = (const T*)F.args[parity].src + (size_t)i * F.ncells + n0;
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(src + min(k * LINE, last)));
-        } else if (F.args[parity].flags) {
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(F.args[parity].flags + n0 + min((t - V::Q * per) * 128u, last)));
+        const T* src = (const T*)F.args[parity].src;
+        uint32_t lines;                                              // population lines of the tile
+        if constexpr (CH) {
+            static_assert(CHUNK == LINE, "a chunk slot is one line");
+            const uint32_t c0 = n0 / CHUNK, c1 = (n0 + last) / CHUNK;
+            lines = (c1 - c0 + 1u) * (uint32_t)V::Q;
+            if (t < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + ((size_t)c0 * V::Q * CHUNK + (size_t)t * LINE)));
+        } else {
+            // lines per population range: one more than whole lines, for a
+            // range that does not start on a line boundary
+            const uint32_t per = (blockDim.x + LINE - 1) / LINE + 1;
+            lines = V::Q * per;
+            if (t < lines) {
+                const uint32_t i = t / per, k = t - i * per;
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(src + (size_t)i * F.ncells + n0 + min(k * LINE, last)));
+            }
         }
+        if (t >= lines && t < lines + 2u && F.args[parity].flags)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(F.args[parity].flags + n0 + min((t - lines) * 128u, last)));
     }
 }
 
@@ -809,7 +819,7 @@ template <class V, int COLL, int FMT, class R, int SCHEME, class IX, bool CH = f
 __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : (COLL == 2 ? 3 : 4)) k_ensemble_step(const EnsMember<R>* __restrict__ members,
                                                         const uint32_t* __restrict__ tile_member, int parity) {
     const EnsMember<R>& M = members[__ldg(tile_member + blockIdx.x)];
-    prefetch_tile_ahead<V, FMT>(members, tile_member, parity, M.args[parity].pf);
+    prefetch_tile_ahead<V, FMT, CH>(members, tile_member, parity, M.args[parity].pf);
     const uint32_t n = (blockIdx.x - M.tile0) * blockDim.x + threadIdx.x;
     if (n >= M.ncells) return;
     const StepArgs<R> a = M.args[parity];
@@ -903,8 +913,10 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
     if (!__any_sync(0xffffffffu, (pl | bb) != 0u)) return;
     const uint16_t* src = (const uint16_t*)a.src;
     uint16_t* dst = (uint16_t*)a.dst;
-    // last even element start of the copy (chunked: padded to whole chunks)
-    const uint32_t qN2 = (uint32_t)V::Q * (CH ? ((N + 63u) & ~63u) : N) - 2u;
+    // start of the copy's last whole aligned word (chunked: padded to whole
+    // chunks; structure of arrays: q N may be odd, the last code then has no
+    // aligned partner and the clamp stops one word earlier)
+    const uint32_t qN2 = ((uint32_t)V::Q * (CH ? ((N + 63u) & ~63u) : N) - 2u) & ~1u;
     uint32_t g[V::Q];
     static_for<0, V::Q>([&](auto I) {
         constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);

@@ -113,7 +113,9 @@ def test_paired_ensemble_open_faces_and_every_cell_kind():
     the paired launch, the listed cells the list launch; the result equals
     one launch per member bit for bit."""
     import paper_2112_08926_gb300 as P
-    shapes = [(7, 9, 11), (6, 10, 64), (5, 5, 33), (12, 3, 17)]
+    # (9, 3, 5): odd q N, and the last run's lanes past the member read
+    # source elements beyond the copy (clamped to its last aligned word)
+    shapes = [(7, 9, 11), (6, 10, 64), (5, 5, 33), (12, 3, 17), (9, 3, 5)]
 
     def members():
         out = []
@@ -134,6 +136,42 @@ def test_paired_ensemble_open_faces_and_every_cell_kind():
         eb.step_each(70)
         for ga, gb in zip(a, b):
             assert np.array_equal(ga.f(), gb.f()), layout
+
+
+def test_members_on_their_own_streams():
+    """Members created on different streams: the ensemble's launches wait
+    for the members' initialisation and layout changes, and the members'
+    readbacks on their own streams wait for the ensemble's steps."""
+    import paper_2112_08926_gb300 as P
+    specs = W.ensemble_cavities(count=6, n_min=6, n_max=20, seed=11)
+    streams = [torch.cuda.Stream() for _ in range(3)]
+
+    def members(on_streams):
+        out = []
+        for k, s in enumerate(specs):
+            st = streams[k % 3].cuda_stream if on_streams else None
+            g = P.Lattice(s.n, s.n, s.n, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=s.tau, stream=st)
+            flags, node_u = W.cavity(s.n, s.u_lid)
+            g.set_geometry(flags, node_u)
+            g.set_rho_u(*W.random_fields((s.n, s.n, s.n), seed=s.n))
+            out.append(g)
+        return out
+
+    a, b = members(True), members(False)
+    ea, eb = P.Ensemble(a), P.Ensemble(b)
+    ea.step(70)
+    eb.step(70)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
+    ea.set_layout("chunked")
+    ea.set_variant("paired", 2)
+    ea.step(66)
+    eb.step_each(66)
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
+    ea.close()
+    for ga, gb in zip(a, b):
+        assert np.array_equal(ga.f(), gb.f())
 
 
 def test_paired_ensemble_members_match_oracle():
@@ -177,6 +215,16 @@ def test_member_stepped_outside_is_detected():
     with pytest.raises(P.LBMError) as ei:
         e.step(1)
     assert ei.value.status == 7
+    # a member whose copies changed outside (A-A keeps one copy): the
+    # ensemble's tables no longer hold its buffers and it refuses to step
+    mem2 = make_members(specs, "FP32", "AB", P)
+    e2 = P.Ensemble(mem2)
+    e2.step(2)
+    mem2[1].set_scheme("AA")
+    with pytest.raises(P.LBMError) as ei:
+        e2.step(1)
+    assert ei.value.status == 7
+    e2.close()
 
 
 def _full_ensemble(P, specs, storage, arith):
