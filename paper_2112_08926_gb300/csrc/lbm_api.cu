@@ -56,6 +56,13 @@ template <class R> void make_relax(const lbm_params& p, Relax<R>& k) {
     k.cs = (R)(1.0 / std::sqrt(3.0));
     for (int a = 0; a < 3; ++a) k.F[a] = (R)p.force[a];
     k.force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;
+    // force components that keep a nonzero numerator j_a + F_a/2 of the
+    // 16-bit formats at or above 2^-100 in magnitude (numerators_ok)
+    k.xsafe = 1;
+    for (int a = 0; a < 3; ++a) {
+        const double fa = std::fabs((double)k.F[a]);
+        if (fa != 0.0 && (fa < 0x1p-76 || fa > 0x1p90)) k.xsafe = 0;
+    }
     k.sh = p.no_ddf_shifting ? (R)0 : (R)1;
     if (p.collision == LBM_MRT) {   // D3Q19 rates of d'Humieres et al. (2002); shear and conserved: omega
         const double om = 1.0 / p.tau;

@@ -447,6 +447,7 @@ template <class R> struct Relax {
     R F[3];
     R sh;
     int force;
+    int xsafe;                // every F_a is 0 or 2^-76 <= |F_a| <= 2^90 (see numerators_ok)
     R mrt_r[19], mrt_p[19];   // MRT: s_k / |M_k|^2 and (1 - s_k / 2) / |M_k|^2 (D3Q19)
 };
 
@@ -548,23 +549,24 @@ __device__ __forceinline__ void moments(const R* g, R& rho, R* j, R sh) {
 // one ulp (faithful), so x - rho q1 is exact, and by Markstein's theorem
 // (P. Markstein, IBM J. Res. Dev. 34 (1990) 111: a faithful quotient
 // corrected with the correctly rounded reciprocal) u is the correctly rounded
-// quotient -- provided nothing underflows or overflows, which holds for
-// |x| in [2^-80, 2^80] and rho in [2^-20, 2^20] (FP64: 2^-800, 2^800 and
-// 2^-200, 2^200).  A zero x gives +0; the sign of x is copied back.  Outside
-// those ranges the IEEE division itself is taken.  (Three IEEE divisions give
-// the same bits; on lattices at rest they ran much slower.)
+// quotient -- provided nothing overflows and no residual falls below the
+// normal range.  A residual of a faithful quotient is a multiple of
+// ulp(q) ulp(rho) >= 2^(e_x - 47), so |x| in [2^-100, 2^100] with rho in
+// [2^-20, 2^20] keeps every intermediate normal and exact (FP64: 2^-800,
+// 2^800 and 2^-200, 2^200).  A zero x gives a zero of the right sign once the
+// sign of x is copied back.  Outside those ranges the IEEE division itself is
+// taken.  (Three IEEE divisions give the same bits; on lattices at rest they
+// ran much slower.)
 template <class R> struct DivRange;
 template <> struct DivRange<float> {
-    static constexpr float xlo = 0x1p-80f, xhi = 0x1p80f, rlo = 0x1p-20f, rhi = 0x1p20f;
+    static constexpr float xlo = 0x1p-100f, xhi = 0x1p100f, rlo = 0x1p-20f, rhi = 0x1p20f;
 };
 template <> struct DivRange<double> {
     static constexpr double xlo = 0x1p-800, xhi = 0x1p800, rlo = 0x1p-200, rhi = 0x1p200;
 };
 
 template <class R>
-__device__ __forceinline__ R div_corrected(R x, R rho, R y, bool& ok) {
-    const R ax = fabs(x);
-    ok = ok && (x == R(0) || (ax >= DivRange<R>::xlo && ax <= DivRange<R>::xhi));
+__device__ __forceinline__ R div_corrected(R x, R rho, R y) {
     const R q0 = x * y;
     const R q1 = fmaR(fmaR(-q0, rho, x), y, q0);
     return copysign(fmaR(fmaR(-q1, rho, x), y, q1), x);
@@ -573,6 +575,32 @@ __device__ __forceinline__ R div_corrected(R x, R rho, R y, bool& ok) {
 template <class R>
 __device__ __forceinline__ bool rho_in_range(R rho) {
     return rho >= DivRange<R>::rlo && rho <= DivRange<R>::rhi;
+}
+
+// Whether the three numerators lie where div_corrected is exact.  In general
+// each one is 0 or within [xlo, xhi].  XS: populations decoded from a 16-bit
+// code (FP32 arithmetic).  Every value such a code decodes to is a multiple
+// of the format's smallest magnitude (FP16 2^-24, FP16S 2^-24 before its
+// 2^-15 scale, FP16C and the posits 2^-59 at the least) and FP32 sums of such
+// multiples stay multiples, so a nonzero j_a 2^-SL is at least 2^-59 in
+// magnitude; with k.xsafe the force adds a multiple of 2^-100 (|F_a| >= 2^-76)
+// that keeps a nonzero x_a at or above 2^-100.  Only the upper bound is then
+// open -- an FP16 code may decode to infinity -- and one comparison of the
+// largest magnitude settles it.  A NaN numerator escapes the maximum, but
+// gives a NaN quotient on both routes, which the clamp that follows maps to
+// the same value.
+template <class R, bool XS>
+__device__ __forceinline__ bool numerators_ok(const Relax<R>& k, const R* x) {
+    if constexpr (XS) {
+        if (k.xsafe) return maxR(maxR(fabs(x[0]), fabs(x[1])), fabs(x[2])) <= DivRange<R>::xhi;
+    }
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const R ax = fabs(x[a]);
+        ok = ok && (x[a] == R(0) || (ax >= DivRange<R>::xlo && ax <= DivRange<R>::xhi));
+    }
+    return ok;
 }
 
 // the numerators x_a = j_a 2^-SL (+ F_a / 2); j is the scaled momentum and
@@ -586,14 +614,14 @@ __device__ __forceinline__ void numerators(const Relax<R>& k, const R* j, R* x) 
     }
 }
 
-template <class R, int SL>
+template <class R, int SL, bool XS = false>
 __device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R* u) {
     R x[3];
     numerators<R, SL>(k, j, x);
     const R y = R(1) / rho;
-    bool ok = rho_in_range(rho);
+    const bool ok = rho_in_range(rho) && numerators_ok<R, XS>(k, x);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = div_corrected(x[a], rho, y, ok);
+    for (int a = 0; a < 3; ++a) u[a] = div_corrected(x[a], rho, y);
     if (!ok) {
 #pragma unroll
         for (int a = 0; a < 3; ++a) u[a] = x[a] / rho;
@@ -602,18 +630,19 @@ __device__ __forceinline__ void velocity(const Relax<R>& k, R rho, const R* j, R
 
 // the same for two cells, whose reciprocals and corrections overlap; one
 // fallback for both
-template <class R, int SL>
+template <class R, int SL, bool XS = false>
 __device__ __forceinline__ void velocity_pair(const Relax<R>& k, R ra, const R* ja, R* ua, R rb, const R* jb,
                                               R* ub) {
     R xa[3], xb[3];
     numerators<R, SL>(k, ja, xa);
     numerators<R, SL>(k, jb, xb);
     const R ya = R(1) / ra, yb = R(1) / rb;
-    bool ok = rho_in_range(ra) && rho_in_range(rb);
+    const bool ok = rho_in_range(ra) && rho_in_range(rb) && numerators_ok<R, XS>(k, xa) &&
+                    numerators_ok<R, XS>(k, xb);
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        ua[a] = div_corrected(xa[a], ra, ya, ok);
-        ub[a] = div_corrected(xb[a], rb, yb, ok);
+        ua[a] = div_corrected(xa[a], ra, ya);
+        ub[a] = div_corrected(xb[a], rb, yb);
     }
     if (!ok) {
 #pragma unroll
@@ -741,12 +770,13 @@ __device__ __forceinline__ void clamp_u(const Relax<R>& k, R* u) {
     for (int a = 0; a < 3; ++a) u[a] = minR(maxR(u[a], -k.cs), k.cs);
 }
 
-// one stream-collide update: moments, velocity, clamp, equilibrium, collision
-template <class V, int COLL, class R, int SL>
+// one stream-collide update: moments, velocity, clamp, equilibrium,
+// collision; XS: populations decoded from 16-bit codes (see numerators_ok)
+template <class V, int COLL, class R, int SL, bool XS = false>
 __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
     R rho, j[3], u[3];
     moments<V, R, SL>(f, rho, j, k.sh);
-    velocity<R, SL>(k, rho, j, u);
+    velocity<R, SL, XS>(k, rho, j, u);
     clamp_u(k, u);
     collide_post<V, COLL, R, SL>(k, f, rho, u);
 }
@@ -754,12 +784,12 @@ __device__ __forceinline__ void collide(const Relax<R>& k, R* f) {
 // two cells: the density and velocity of both first, so that their
 // dependent chains (sums, reciprocal, corrections) overlap, then each cell's
 // equilibrium and collision; the same values as two collide() calls
-template <class V, int COLL, class R, int SL>
+template <class V, int COLL, class R, int SL, bool XS = false>
 __device__ __forceinline__ void collide_pair(const Relax<R>& k, R* fa, R* fb) {
     R ra, rb, ja[3], jb[3], ua[3], ub[3];
     moments<V, R, SL>(fa, ra, ja, k.sh);
     moments<V, R, SL>(fb, rb, jb, k.sh);
-    velocity_pair<R, SL>(k, ra, ja, ua, rb, jb, ub);
+    velocity_pair<R, SL, XS>(k, ra, ja, ua, rb, jb, ub);
     clamp_u(k, ua);
     clamp_u(k, ub);
     collide_post<V, COLL, R, SL>(k, fa, ra, ua);

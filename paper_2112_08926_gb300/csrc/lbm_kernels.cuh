@@ -252,7 +252,7 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
             walls = gather<V, FMT, R, FLAGS, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
         else if (FLAGS && (fl & (PH == LAYOUT_AA_NATURAL ? F_NEAR_MOVING : F_NEAR_SOLID)))
             walls = gather<V, FMT, R, true, LAYOUT, IX>(a, src, x, y, z, n, fl, f);
-        collide<V, COLL, R, S::SL>(a.k, f);
+        collide<V, COLL, R, S::SL, (FMT >= 2)>(a.k, f);
     }
     if constexpr (SCHEME == SCHEME_AB) {
         static_for<0, V::Q>([&](auto I) { S::template store_g<R>(elem_ptr<IX, CH, V>(dst, I.value, a.N, n), 0u, f[I.value]); });
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(512, 2) k_step_staged(const StepArgs<float> a,
                 const int xs = cx == 0 ? x : (cx > 0 ? xm : xp);
                 f[i] = S::template load_g<float>(tile, (uint32_t)(i * H * NX + xs));
             });
-            collide<V, COLL, float, S::SL>(a.k, f);
+            collide<V, COLL, float, S::SL, (FMT >= 2)>(a.k, f);
             const uint32_t n = (uint32_t)z * plane + (uint32_t)y * NX + x;
             static_for<0, V::Q>([&](auto I) { S::template store_g<float>(dst, (uint32_t)I.value * N + n, f[I.value]); });
         }
@@ -501,14 +501,14 @@ __global__ void __launch_bounds__(256, 3) k_step_pair(const StepArgs<float> a) {
             f[I.value] = C::dec_g(g[I.value] & 0xFFFFu);
             fb[I.value] = C::dec_g(g[I.value] >> 16);
         });
-        collide_pair<V, COLL, float, SL>(a.k, f, fb);
+        collide_pair<V, COLL, float, SL, (FMT >= 2)>(a.k, f, fb);
         static_for<0, V::Q>([&](auto I) { g[I.value] = C::enc_g(f[I.value]) | (C::enc_g(fb[I.value]) << 16); });
     } else {
         static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] & 0xFFFFu); });
-        collide<V, COLL, float, SL>(a.k, f);
+        collide<V, COLL, float, SL, (FMT >= 2)>(a.k, f);
         static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFF0000u) | C::enc_g(f[I.value]); });
         static_for<0, V::Q>([&](auto I) { f[I.value] = C::dec_g(g[I.value] >> 16); });
-        collide<V, COLL, float, SL>(a.k, f);
+        collide<V, COLL, float, SL, (FMT >= 2)>(a.k, f);
         static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFFu) | (C::enc_g(f[I.value]) << 16); });
     }
     if (active) {
@@ -696,16 +696,16 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
         else fa[I.value] = PC::dec(g[I.value]).x;
     });
     if constexpr (SEQ) {
-        collide<V, COLL, float, SL>(a.k, fa);
+        collide<V, COLL, float, SL, (FMT >= 2)>(a.k, fa);
         static_for<0, V::Q>([&](auto I) {
             g[I.value] = (g[I.value] & 0xFFFF0000u) | enc1(fa[I.value]);
             fa[I.value] = Codec16<FMT>::dec_g(g[I.value] >> 16);
         });
-        collide<V, COLL, float, SL>(a.k, fa);
+        collide<V, COLL, float, SL, (FMT >= 2)>(a.k, fa);
         static_for<0, V::Q>([&](auto I) { g[I.value] = (g[I.value] & 0xFFFFu) | (enc1(fa[I.value]) << 16); });
     } else {
         static_for<0, V::Q>([&](auto I) { fb[I.value] = PC::dec(g[I.value]).y; });
-        collide_pair<V, COLL, float, SL>(a.k, fa, fb);
+        collide_pair<V, COLL, float, SL, (FMT >= 2)>(a.k, fa, fb);
     }
     // the new code pair of population i
     auto pair = [&](auto I) -> uint32_t {
@@ -788,6 +788,11 @@ __device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restri
         const uint32_t ft = blockIdx.x + (uint32_t)pf;
         if (pf <= 0 || ft >= gridDim.x) return;
         const uint32_t t = threadIdx.x;
+        // threads beyond the most lines a tile can need leave before the
+        // member lookup (a tile of blockDim cells spans at most
+        // blockDim / 64 + 2 chunks; a population range at most `per` lines)
+        const uint32_t per = (blockDim.x + LINE - 1) / LINE + 1;
+        if (t >= (CH ? (blockDim.x / CHUNK + 2u) * (uint32_t)V::Q : (uint32_t)V::Q * per) + 2u) return;
         const EnsMember<R>& F = members[__ldg(tile_member + ft)];
         const uint32_t n0 = (ft - F.tile0) * blockDim.x;
         const uint32_t last = min(blockDim.x, F.ncells - n0) - 1;   // tile ft holds cells n0 .. n0 + last
@@ -799,9 +804,8 @@ __device__ __forceinline__ void prefetch_tile_ahead(const EnsMember<R>* __restri
             lines = (c1 - c0 + 1u) * (uint32_t)V::Q;
             if (t < lines) asm volatile("prefetch.global.L2 [%0];" ::"l"(src + ((size_t)c0 * V::Q * CHUNK + (size_t)t * LINE)));
         } else {
-            // lines per population range: one more than whole lines, for a
-            // range that does not start on a line boundary
-            const uint32_t per = (blockDim.x + LINE - 1) / LINE + 1;
+            // `per` lines per population range: one more than whole lines, for
+            // a range that does not start on a line boundary
             lines = V::Q * per;
             if (t < lines) {
                 const uint32_t i = t / per, k = t - i * per;
@@ -964,7 +968,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
         fb[I.value] = v.y;
     });
     const Relax<float> k = a.k;                                   // the member's constants in registers
-    collide_pair<V, COLL, float, SL>(k, fa, fb);
+    collide_pair<V, COLL, float, SL, (FMT >= 2)>(k, fa, fb);
     // Every other half is written: the listed cells' halves carry values the
     // list launch that follows overwrites, so the stores are whole words,
     // the skipped halves masked to zero, except where a word would reach

@@ -659,3 +659,50 @@ def test_stream_auto_picks_a_scheme_and_keeps_results():
     assert np.array_equal(g.f(), ref.f())
     g.close()
     ref.close()
+
+
+def _quotient_edge_populations(nz, ny, nx, big):
+    """Shifted D3Q19 populations whose cells reach every branch of the
+    velocity quotient: ordinary values, exact zeros (numerators 0 of either
+    sign), a density below 2^-20 (f_0 = -1 plus one 2^-22), a negative
+    density, and large values (FP16: 6e4)."""
+    rng = np.random.default_rng(17)
+    f = rng.uniform(-0.01, 0.01, (19, nz, ny, nx))
+    flat = f.reshape(19, -1)
+    n = flat.shape[1]
+    flat[:, 0:n:7] = 0.0                          # at rest: zero momenta
+    flat[1:, 1:n:7] = -0.0
+    flat[:, 2:n:7] = 0.0                          # rho = 2^-22
+    flat[0, 2:n:7] = -1.0
+    flat[1, 2:n:7] = 2.0 ** -22
+    flat[0, 3:n:7] = -1.5                         # rho < 0
+    flat[0, 4:n:7] = big                          # large density and momentum
+    flat[1, 4:n:7] = big / 2
+    return f
+
+
+@pytest.mark.parametrize("storage", ["FP16", "FP16S", "P16_2C", "FP32"])
+@pytest.mark.parametrize("force", [(0.0, 0.0, 0.0), (1e-30, 0.0, 2e-5), (2.0 ** -76, -(2.0 ** -70), 0.0),
+                                   (-(2.0 ** 90), 0.0, 1e-3)])
+@pytest.mark.parametrize("nx", [64, 6])
+def test_velocity_quotient_ranges_bitwise(storage, force, nx):
+    """u_a = (j_a + F_a/2) / rho is the IEEE quotient on every route: the
+    corrected reciprocal, the 16-bit storage shortcut that checks only the
+    largest numerator (force components 0 or within [2^-76, 2^90]), and the
+    division taken for numerators below 2^-100 (a 1e-30 force), densities
+    outside [2^-20, 2^20] and non-finite values.  Bit for bit against the
+    oracle after one and two steps, on the paired (nx = 64) and the generic
+    (nx = 6) kernels."""
+    nz, ny = 3, 5
+    big = 6.0e4 if storage in ("FP16", "FP32") else 1.5
+    f = _quotient_edge_populations(nz, ny, nx, big)
+    g = P().Lattice(nx, ny, nz, "D3Q19", "SRT", storage, "FP32", "AB", tau=0.8, force=force)
+    g.set_f(f)
+    o = oracle.Lattice(nx, ny, nz, "D3Q19", "SRT", "ORD32", storage, tau=0.8, force=force)
+    o.set_f(f)
+    assert np.array_equal(g.f(), o.f(), equal_nan=True)
+    for _ in range(2):
+        g.step(1)
+        o.step(1)
+        assert np.array_equal(g.f(), o.f(), equal_nan=True)
+    g.close()
