@@ -169,6 +169,7 @@ struct Ordered {
     const VelSet& vs;
     R w[27], k6[27], w3[27];
     R om, c1, omp, omm, cSp, cSm, cs, F[3];
+    R omph, ommh, cSph, cSmh;   // the TRT rates and source factors halved (exact)
     R sh;   /* 1: shifted populations, 0: unshifted */
     bool force;
 
@@ -185,6 +186,10 @@ struct Ordered {
         omm = (R)(1.0 / (lam / (L->p.tau - 0.5) + 0.5));
         cSp = (R)1 - (R)0.5 * omp;
         cSm = (R)1 - (R)0.5 * omm;
+        omph = (R)0.5 * omp;
+        ommh = (R)0.5 * omm;
+        cSph = (R)0.5 * cSp;
+        cSmh = (R)0.5 * cSm;
         cs = (R)(1.0 / std::sqrt(3.0));
         for (int a = 0; a < 3; ++a) F[a] = (R)L->p.force[a];
         force = L->has_force();
@@ -336,16 +341,19 @@ struct Ordered {
             f[0] = fmaR(-omp, a0, force ? fmaR(cSp, S[0], f[0]) : f[0]);
             for (int p = 1; p < vs.q; p += 2) {
                 const int q = p + 1;
+                // symmetric and antisymmetric parts of the pair, (a + b)/2 and
+                // (a - b)/2, relaxed with omega+ and omega-; the halves ride
+                // on the rates: omega/2 (a + b) is one product, exact halving
                 const R a = f[p] - feq[p], b = f[q] - feq[q];
-                const R sp = (R)0.5 * (a + b), sm = (R)0.5 * (a - b);
+                const R s = a + b, d = a - b;
                 R fp = f[p], fq = f[q];
-                if (force) {
-                    const R Sp = (R)0.5 * (S[p] + S[q]), Sm = (R)0.5 * (S[p] - S[q]);
-                    fp = fp + fmaR(cSm, Sm, cSp * Sp);
-                    fq = fq + fmaR(-cSm, Sm, cSp * Sp);
+                if (force) {   // (1 - omega+/2) and (1 - omega-/2) on the source's parts
+                    const R Ss = S[p] + S[q], Sd = S[p] - S[q];
+                    fp = fp + fmaR(cSmh, Sd, cSph * Ss);
+                    fq = fq + fmaR(-cSmh, Sd, cSph * Ss);
                 }
-                f[p] = fmaR(-omm, sm, fmaR(-omp, sp, fp));
-                f[q] = fmaR(omm, sm, fmaR(-omp, sp, fq));
+                f[p] = fmaR(-ommh, d, fmaR(-omph, s, fp));
+                f[q] = fmaR(ommh, d, fmaR(-omph, s, fq));
             }
         }
     }

@@ -53,6 +53,10 @@ template <class R> void make_relax(const lbm_params& p, Relax<R>& k) {
     k.omm = (R)(1.0 / (p.trt_lambda / (p.tau - 0.5) + 0.5));
     k.cSp = (R)1 - (R)0.5 * k.omp;
     k.cSm = (R)1 - (R)0.5 * k.omm;
+    k.omph = (R)0.5 * k.omp;
+    k.ommh = (R)0.5 * k.omm;
+    k.cSph = (R)0.5 * k.cSp;
+    k.cSmh = (R)0.5 * k.cSm;
     k.cs = (R)(1.0 / std::sqrt(3.0));
     for (int a = 0; a < 3; ++a) k.F[a] = (R)p.force[a];
     k.force = (p.force[0] != 0.0 || p.force[1] != 0.0 || p.force[2] != 0.0) ? 1 : 0;

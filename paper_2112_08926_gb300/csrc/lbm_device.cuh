@@ -444,6 +444,7 @@ __device__ __forceinline__ double maxR(double a, double b) { return fmax(a, b); 
 // same formulas with rho = sum f and D = w rho give the plain equilibrium.
 template <class R> struct Relax {
     R om, c1, omp, omm, cSp, cSm, cs;
+    R omph, ommh, cSph, cSmh;   // TRT: omega+/2, omega-/2, (1 - omega+/2)/2, (1 - omega-/2)/2 (exact halves)
     R F[3];
     R sh;
     int force;
@@ -749,16 +750,18 @@ __device__ __forceinline__ void collide_post(const Relax<R>& k, R* f, R rho, con
         f[0] = fmaR(-k.omp, a0, k.force ? fmaR(k.cSp, S[0], f[0]) : f[0]);
         static_for<0, (V::Q - 1) / 2>([&](auto K) {
             constexpr int p = 2 * K.value + 1, q = p + 1;
+            // parts (a + b)/2 and (a - b)/2 relaxed with omega+ and omega-,
+            // the halves carried by the rates (one product, exact halving)
             const R a = f[p] - feq[p], b = f[q] - feq[q];
-            const R sp = R(0.5) * (a + b), sm = R(0.5) * (a - b);
+            const R s = a + b, d = a - b;
             R fp = f[p], fq = f[q];
             if (k.force) {
-                const R Sp = R(0.5) * (S[p] + S[q]), Sm = R(0.5) * (S[p] - S[q]);
-                fp = fp + fmaR(k.cSm, Sm, k.cSp * Sp);
-                fq = fq + fmaR(-k.cSm, Sm, k.cSp * Sp);
+                const R Ss = S[p] + S[q], Sd = S[p] - S[q];
+                fp = fp + fmaR(k.cSmh, Sd, k.cSph * Ss);
+                fq = fq + fmaR(-k.cSmh, Sd, k.cSph * Ss);
             }
-            f[p] = fmaR(-k.omm, sm, fmaR(-k.omp, sp, fp));
-            f[q] = fmaR(k.omm, sm, fmaR(-k.omp, sp, fq));
+            f[p] = fmaR(-k.ommh, d, fmaR(-k.omph, s, fp));
+            f[q] = fmaR(k.ommh, d, fmaR(-k.omph, s, fq));
         });
     }
 }
