@@ -728,11 +728,18 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
             else *reinterpret_cast<uint32_t*>(out + slot * CHUNK) = w;
         });
     } else {
-        // push slot i into the destination row (y + c_y, z + c_z)
+        // push slot i into the destination row (y + c_y, z + c_z): its chunk
+        // lies dy[c_y] + dz[c_z] chunks from this cell's own (periodic; |dy +
+        // dz| < N / 64 < 2^25), four offsets kept through the collision
+        // instead of the row indices
         const uint32_t pl_up = __shfl_up_sync(0xffffffffu, pl, 1), pl_dn = __shfl_down_sync(0xffffffffu, pl, 1);
+        const int32_t rowc = (int32_t)XT, planec = (int32_t)(ny * XT);
+        const int32_t dy[3] = {y == 0 ? (a.ny - 1) * rowc : -rowc, 0, y == a.ny - 1 ? -(a.ny - 1) * rowc : rowc};
+        const int32_t dz[3] = {z == 0 ? (a.nz - 1) * planec : -planec, 0, z == a.nz - 1 ? -(a.nz - 1) * planec : planec};
+        uint16_t* const base = dst + (size_t)own_chunk * CHE;
         static_for<0, V::Q>([&](auto I) {
             constexpr int i = I.value, cx = V::c(i, 0), cy = V::c(i, 1), cz = V::c(i, 2);
-            uint16_t* rowp = dst + (size_t)((ry[1 + cy] + rz[1 + cz]) * XT + X) * CHE + i * CHUNK;
+            uint16_t* rowp = base + (int64_t)(dy[1 + cy] + dz[1 + cz]) * (int64_t)CHE + i * CHUNK;
             const uint32_t own = pair(I);
             if constexpr (cx == 0) {
                 if constexpr (PLAIN) put(rowp, 2 * lane, own, pl);
