@@ -286,6 +286,55 @@ def run_ensemble(P, torch, steps, warmup, count=512, seed=20211216):
             "speedup": t_e / t_b, "launches_per_step": {"batched": 2, "per_launch": 2 * count}}
 
 
+def small_ensembles(P, torch, steps, warmup, edges=(32, 48, 64), total=256 ** 3):
+    """Small lattices alone fill little of the GPU: for each edge n, one FP16S
+    lid-driven cavity n^3 (D3Q19 SRT, CUDA graphs of 32 steps) against an
+    ensemble of equal members with about `total` cells in all (member layout,
+    kernel, tile and scheme autotuned), both timed with CUDA events."""
+    import workloads as W
+    peak, _ = peaks()
+    bpc = 2 * 19 * 2 + 1
+    rows = []
+    for n in edges:
+        count = max(1, total // n ** 3)
+
+        def member():
+            g = P.Lattice(n, n, n, "D3Q19", "SRT", "FP16S", "FP32", "AB", tau=0.6)
+            flags, node_u = W.cavity(n, 0.1)
+            g.set_geometry(flags, node_u)
+            g.set_rho_u()
+            return g
+
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        one = member()
+        one.step(64)
+        torch.cuda.synchronize()
+        ev[0].record(); one.step(steps); ev[1].record()
+        torch.cuda.synchronize()
+        t_one = ev[0].elapsed_time(ev[1]) / 1e3
+        one.close()
+        mem = [member() for _ in range(count)]
+        e = P.Ensemble(mem)
+        bx, by = e.autotune(trial_steps=3)
+        e.step(max(warmup, 64))
+        torch.cuda.synchronize()
+        ev[0].record(); e.step(steps); ev[1].record()
+        torch.cuda.synchronize()
+        t_ens = ev[0].elapsed_time(ev[1]) / 1e3
+        layout, kernel, scheme = e.layout(), e.variant(), e.scheme()
+        e.close()
+        for g in mem:
+            g.close()
+        cells = count * n ** 3
+        rows.append({"edge": n, "members": count, "cells": cells, "steps": steps,
+                     "single_mlups": n ** 3 * steps / t_one / 1e6,
+                     "single_frac_hbm": bpc * n ** 3 * steps / t_one / 1e9 / peak,
+                     "ensemble_mlups": cells * steps / t_ens / 1e6,
+                     "ensemble_frac_hbm": bpc * cells * steps / t_ens / 1e9 / peak,
+                     "tile": [bx, by], "layout": layout, "kernel": kernel, "scheme": scheme})
+    return rows
+
+
 def cavity_sweep(P, torch, steps, formats=("FP32", "FP16S", "FP16C"), re=1000.0, u_lid=0.1, only=None,
                  with_oracle=True):
     """D3Q19 TRT lid-driven cavities N^3 (wall shell included, lid z = N-1
@@ -489,6 +538,8 @@ def main():
                     help="D2Q9 / D3Q19 / D3Q27 throughput per storage format instead of the default run")
     ap.add_argument("--karman", action="store_true",
                     help="only the Karman vortex street accuracy run (Strouhal number, L2 vs FP64)")
+    ap.add_argument("--small-ensembles", action="store_true",
+                    help="only small cavities alone against ensembles of equal members")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -520,6 +571,11 @@ def main():
     if args.karman:
         if rank == 0:
             print(json.dumps({"karman": karman(P, torch)}), flush=True)
+        return
+
+    if args.small_ensembles:
+        if rank == 0:
+            print(json.dumps({"small_ensembles": small_ensembles(P, torch, args.steps, args.warmup)}), flush=True)
         return
 
     if args.cavity_sweep:
