@@ -364,6 +364,10 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         h->flags = (uint8_t*)h->alloc(N);
         if (!h->flags) return h->fail(LBM_ERR_OOM, "flags");
     }
+    if (!h->walls) {
+        h->walls = (uint32_t*)h->alloc(N * sizeof(uint32_t));
+        if (!h->walls) return h->fail(LBM_ERR_OOM, "wall masks");
+    }
     if (h->cuda(cudaMemcpyAsync(h->flags, flags, N, cudaMemcpyHostToDevice, h->stream), "flags upload"))
         return LBM_ERR_CUDA;
     h->has_open_boundaries = any_open;
@@ -399,9 +403,12 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
     }
     {
         const int grid = (int)std::min<size_t>((N + 255) / 256, 152 * 16);
-        if (h->p.velset == LBM_D2Q9) k_mark_neighbours<D2Q9><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
-        else if (h->p.velset == LBM_D3Q19) k_mark_neighbours<D3Q19><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
-        else k_mark_neighbours<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->p.nx, h->p.ny, h->p.nz);
+        if (h->p.velset == LBM_D2Q9)
+            k_mark_neighbours<D2Q9><<<grid, 256, 0, h->stream>>>(h->flags, h->walls, h->p.nx, h->p.ny, h->p.nz);
+        else if (h->p.velset == LBM_D3Q19)
+            k_mark_neighbours<D3Q19><<<grid, 256, 0, h->stream>>>(h->flags, h->walls, h->p.nx, h->p.ny, h->p.nz);
+        else
+            k_mark_neighbours<D3Q27><<<grid, 256, 0, h->stream>>>(h->flags, h->walls, h->p.nx, h->p.ny, h->p.nz);
         if (h->cuda(cudaGetLastError(), "mark kernel")) return LBM_ERR_CUDA;
     }
     {   // list of the non-plain cells (two passes: count, then fill): the

@@ -25,6 +25,7 @@ struct lbm_handle {
     cudaStream_t stream = nullptr;
     void* f[2] = {nullptr, nullptr};
     uint8_t* flags = nullptr;
+    uint32_t* walls = nullptr;   // with flags: per-cell mask of the solid upstream directions (k_mark_neighbours)
     float* node_u = nullptr;
     float* node_rho = nullptr;
     double* scratch = nullptr;
@@ -104,6 +105,7 @@ struct lbm_handle {
         a.src = f[src_index];
         a.dst = aa() ? f[0] : f[1 - src_index];
         a.flags = flags;
+        a.walls = walls;
         a.node_u = node_u;
         a.node_rho = node_rho;
         a.nx = p.nx; a.ny = p.ny; a.nz = p.nz;

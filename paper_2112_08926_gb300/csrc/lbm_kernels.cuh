@@ -53,6 +53,7 @@ template <class R> struct StepArgs {
     const void* src;          // A-B: copy read this step; A-A: the single copy
     void* dst;                // A-B: copy written; A-A: same as src
     const uint8_t* flags;     // NULL for the flag-free periodic kernel
+    const uint32_t* walls;    // with flags: bit i of cell n set if the upstream cell n - c_i is solid
     const float* node_u;      // 3*N, component-major
     const float* node_rho;    // N
     int nx, ny, nz;
@@ -105,14 +106,6 @@ template <class V, int I, class R, int SL>
 __device__ __forceinline__ R moving_term(const float* node_u, size_t N, uint32_t m) {
     const R uw[3] = {(R)node_u[m], (R)node_u[N + m], (R)node_u[2 * N + m]};
     return R(6.0 * V::w(I) * Pow2<SL>::up) * csum<V, I, R>(uw);
-}
-
-// Bit i set: the upstream cell x - c_i of the cell at `nb` is solid.
-template <class V>
-__device__ __forceinline__ uint32_t solid_upstream(const uint8_t* __restrict__ flags, const Nbr& nb) {
-    uint32_t m = 0;
-    static_for<1, V::Q>([&](auto I) { m |= ((uint32_t)flags[nb.up<V, I.value>()] & F_WALL) << I.value; });
-    return m;
 }
 
 // Streamed populations of a cell next to solid cells (or an outflow cell),
@@ -234,8 +227,9 @@ __device__ __forceinline__ void cell_step(const StepArgs<R>& a, int x, int y, in
         // nothing to replace); every other non-plain cell is listed
         if (fl != F_NEAR_SOLID) return;
         if constexpr (PH != LAYOUT_AA_NATURAL) {
-            const Nbr nb(x, y, z, a.nx, a.ny, a.nz);
-            walls = solid_upstream<V>(a.flags, nb);
+            // the wall mask of the cell, then its own populations of the
+            // bounce-back directions
+            walls = a.walls[n];
             static_for<1, V::Q>([&](auto I) {
                 constexpr int i = I.value;
                 constexpr int bslot = PH == LAYOUT_AA_SWAPPED ? i : opposite(i);
@@ -661,22 +655,27 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
     }
     if constexpr (PLAIN && PHASE == LAYOUT_AB) {
         // plain bounce-back: a direction whose upstream cell is solid takes
-        // the code of the cell's own opposite population, from its own row
+        // the code of the cell's own opposite population, from its own row.
+        // Both cells of a lane issue their upstream flag loads, and the lane
+        // its own row's code pairs, before any of them is used, so a warp
+        // with such cells waits for one round trip to memory.
         if (__any_sync(0xffffffffu, bb != 0u)) {
-            const uint16_t* own = src + (size_t)own_chunk * CHE + 2 * lane;
-#pragma unroll 1
-            for (int h = 0; h < 2; ++h) {
-                if (!((bb >> h) & 1u)) continue;
-                const Nbr nb((int)(X * CHUNK) + 2 * lane + h, y, z, a.nx, a.ny, a.nz);
-                const uint32_t walls = solid_upstream<V>(a.flags, nb);
-                static_for<1, V::Q>([&](auto I) {
-                    constexpr int i = I.value;
-                    if ((walls >> i) & 1u) {
-                        const uint32_t c = own[opposite(i) * CHUNK + h];
-                        g[i] = h ? ((g[i] & 0xFFFFu) | (c << 16)) : ((g[i] & 0xFFFF0000u) | c);
-                    }
-                });
-            }
+            const uint32_t* own = reinterpret_cast<const uint32_t*>(src + (size_t)own_chunk * CHE) + lane;
+            // wall masks of cells 2l and 2l+1 (consecutive, the first even: one 8-byte load)
+            const uint32_t n0 = (ry[1] + rz[1]) * (uint32_t)a.nx + X * CHUNK + 2u * (uint32_t)lane;
+            uint2 wm = make_uint2(0u, 0u);
+            if (bb) wm = *reinterpret_cast<const uint2*>(a.walls + n0);
+            if (!(bb & 1u)) wm.x = 0u;
+            if (!(bb & 2u)) wm.y = 0u;
+            static_for<1, V::Q>([&](auto I) {
+                constexpr int i = I.value;
+                const uint32_t w0 = (wm.x >> i) & 1u, w1 = (wm.y >> i) & 1u;
+                if (__any_sync(0xffffffffu, (w0 | w1) != 0u)) {
+                    const uint32_t o = (w0 | w1) ? own[opposite(i) * (CHUNK / 2)] : 0u;   // slot opposite(i), both cells
+                    const uint32_t keep = (w0 ? 0u : 0x0000FFFFu) | (w1 ? 0u : 0xFFFF0000u);
+                    g[i] = (g[i] & keep) | (o & ~keep);
+                }
+            });
         }
     }
     // SEQ: one cell at a time, the first cell's codes going back into g
@@ -956,9 +955,7 @@ __global__ void __launch_bounds__(128, 5) k_ensemble_pair(const EnsMember<float>
         for (int h = 0; h < 2; ++h) {
             if (!((bb >> h) & 1u)) continue;
             const uint32_t c = n + (uint32_t)h;
-            const uint32_t z = M.by_plane.div(c), r = c - z * plane, y = M.by_nx.div(r), x = r - y * (uint32_t)a.nx;
-            const Nbr nb((int)x, (int)y, (int)z, a.nx, a.ny, a.nz);
-            const uint32_t walls = solid_upstream<V>(a.flags, nb);
+            const uint32_t walls = a.walls[c];
             static_for<1, V::Q>([&](auto I) {
                 constexpr int i = I.value;
                 if ((walls >> i) & 1u) {
@@ -1158,20 +1155,31 @@ __global__ void __launch_bounds__(256) k_put(const PutArgs<R> p, int setf) {
 // Sets the internal bits of non-solid cells: F_NEAR_SOLID if any neighbour
 // is solid or the cell is an outflow cell, F_NEAR_MOVING if any neighbour is a
 // moving wall.
+// The wall mask of each cell (bit i: the upstream cell n - c_i is solid; 0
+// for solid cells) goes to walls[n], so that the fast kernels replace the
+// bounce-back directions of a cell from one word instead of q - 1 flag loads.
 template <class V>
-__global__ void k_mark_neighbours(uint8_t* flags, int nx, int ny, int nz) {
+__global__ void k_mark_neighbours(uint8_t* flags, uint32_t* walls, int nx, int ny, int nz) {
     const uint32_t plane = (uint32_t)nx * (uint32_t)ny;
     const uint32_t N = plane * (uint32_t)nz;
     for (uint32_t n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
         const uint32_t fl = flags[n];
-        if (fl & F_WALL) continue;
+        if (fl & F_WALL) {
+            walls[n] = 0u;
+            continue;
+        }
         const int z = (int)(n / plane);
         const uint32_t r = n - (uint32_t)z * plane;
         const int y = (int)(r / (uint32_t)nx);
         const int x = (int)(r - (uint32_t)y * nx);
         const Nbr nb(x, y, z, nx, ny, nz);
-        uint32_t any = 0;
-        static_for<1, V::Q>([&](auto I) { any |= flags[nb.up<V, I.value>()]; });
+        uint32_t any = 0, m = 0;
+        static_for<1, V::Q>([&](auto I) {
+            const uint32_t u = flags[nb.up<V, I.value>()];
+            any |= u;
+            m |= (u & F_WALL) ? (1u << I.value) : 0u;
+        });
+        walls[n] = m;
         // only the user bits of the neighbours are read (other threads add
         // internal bits to the bytes meanwhile)
         uint32_t add = 0;
