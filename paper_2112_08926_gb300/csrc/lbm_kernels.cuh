@@ -612,12 +612,44 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
         pl = (f0 == 0u ? 1u : 0u) | (f1 == 0u ? 2u : 0u);
         // plain bounce-back cells: A-B replaces their wall directions below;
         // the even A-A half treats them as plain; the odd half leaves them
-        // to the list kernel (their pushes into solid cells turn back)
+        // to the list kernel (their pushes into solid cells turn back; doing
+        // that here, with the turned-back pushes masked per direction, made
+        // the in-place cavities 6% slower)
         if constexpr (PHASE != LAYOUT_AA_SWAPPED) {
             bb = (f0 == F_NEAR_SOLID ? 1u : 0u) | (f1 == F_NEAR_SOLID ? 2u : 0u);
             pl |= bb;
         }
         if (!__any_sync(0xffffffffu, pl != 0u)) return;   // nothing to update in this chunk
+    }
+    // Plain bounce-back (flagged A-B): a direction whose upstream cell is
+    // solid takes the code of the cell's own opposite population.  A warp
+    // with such cells copies its own row's code pairs into shared memory by
+    // cp.async, and their lanes load their two wall masks, before the pulls
+    // are issued; both are used after the pulls.  The copies hold no
+    // registers meanwhile, so the pulls stay in flight together as in a warp
+    // without such cells.
+    constexpr bool BBS = PLAIN && PHASE == LAYOUT_AB;
+    // [warp of the block][slot][lane]; the kernel is launched with 32 x 8 threads
+    __shared__ uint32_t bbrow[BBS ? 8 : 1][BBS ? V::Q : 1][32];
+    uint2 wm = make_uint2(0u, 0u);
+    bool anybb = false;
+    if constexpr (BBS) {
+        anybb = __any_sync(0xffffffffu, bb != 0u);
+        if (anybb) {   // every lane of the warp stages (a branch per lane measured slower than the copies it saves)
+            if (bb != 0u) {
+                const uint32_t n0 = (ry[1] + rz[1]) * (uint32_t)a.nx + X * CHUNK + 2u * (uint32_t)lane;   // cell 2l (even)
+                wm = *reinterpret_cast<const uint2*>(a.walls + n0);
+                if (!(bb & 1u)) wm.x = 0u;
+                if (!(bb & 2u)) wm.y = 0u;
+            }
+            const uint32_t* ownw = reinterpret_cast<const uint32_t*>(src + (size_t)own_chunk * CHE) + lane;
+            static_for<1, V::Q>([&](auto I) {
+                const uint32_t sa = (uint32_t)__cvta_generic_to_shared(&bbrow[threadIdx.y][I.value][lane]);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sa), "l"(ownw + I.value * (CHUNK / 2))
+                             : "memory");
+            });
+            asm volatile("cp.async.commit_group;" ::: "memory");
+        }
     }
     uint32_t g[V::Q];   // lo half: cell 2*lane, hi half: cell 2*lane + 1 (of this chunk)
     if constexpr (PHASE == LAYOUT_AA_NATURAL) {
@@ -653,25 +685,14 @@ __global__ void __launch_bounds__(256, V::Q > 19 ? 2 : 3) k_step_pair_chunked(co
             });
         });
     }
-    if constexpr (PLAIN && PHASE == LAYOUT_AB) {
-        // plain bounce-back: a direction whose upstream cell is solid takes
-        // the code of the cell's own opposite population, from its own row.
-        // Both cells of a lane issue their upstream flag loads, and the lane
-        // its own row's code pairs, before any of them is used, so a warp
-        // with such cells waits for one round trip to memory.
-        if (__any_sync(0xffffffffu, bb != 0u)) {
-            const uint32_t* own = reinterpret_cast<const uint32_t*>(src + (size_t)own_chunk * CHE) + lane;
-            // wall masks of cells 2l and 2l+1 (consecutive, the first even: one 8-byte load)
-            const uint32_t n0 = (ry[1] + rz[1]) * (uint32_t)a.nx + X * CHUNK + 2u * (uint32_t)lane;
-            uint2 wm = make_uint2(0u, 0u);
-            if (bb) wm = *reinterpret_cast<const uint2*>(a.walls + n0);
-            if (!(bb & 1u)) wm.x = 0u;
-            if (!(bb & 2u)) wm.y = 0u;
+    if constexpr (BBS) {
+        if (anybb) {
+            asm volatile("cp.async.wait_all;" ::: "memory");   // this lane's copies (each lane reads its own words)
             static_for<1, V::Q>([&](auto I) {
                 constexpr int i = I.value;
                 const uint32_t w0 = (wm.x >> i) & 1u, w1 = (wm.y >> i) & 1u;
-                if (__any_sync(0xffffffffu, (w0 | w1) != 0u)) {
-                    const uint32_t o = (w0 | w1) ? own[opposite(i) * (CHUNK / 2)] : 0u;   // slot opposite(i), both cells
+                if (w0 | w1) {
+                    const uint32_t o = bbrow[threadIdx.y][opposite(i)][lane];   // slot opposite(i), both cells
                     const uint32_t keep = (w0 ? 0u : 0x0000FFFFu) | (w1 ? 0u : 0xFFFF0000u);
                     g[i] = (g[i] & keep) | (o & ~keep);
                 }
