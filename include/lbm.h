@@ -45,7 +45,8 @@ typedef enum {
     LBM_ERR_UNSUPPORTED = 4,  /* valid but unsupported combination */
     LBM_ERR_DIVERGED = 5,     /* FP64 mass check found a non-finite value */
     LBM_ERR_TIMEOUT = 6,      /* a bounded device-side wait ran out */
-    LBM_ERR_STATE = 7         /* handle poisoned by an earlier CUDA error */
+    LBM_ERR_STATE = 7         /* handle poisoned by an earlier CUDA error, or a call that the
+                                 object's state does not allow (see the calls) */
 } lbm_status;
 
 /* velocity sets (Sec. 2.1; D3Q19 main, D2Q9 and D3Q27 variants) */
@@ -345,7 +346,11 @@ typedef struct lbm_ensemble lbm_ensemble;
 lbm_status lbm_ensemble_create(lbm_handle* const* members, int count, lbm_ensemble** out);
 /* Advance every member nsteps steps: per step one launch over the plain
  * cells of all members and one over the listed boundary cells of all
- * members, replayed from a CUDA graph of up to 64 steps. */
+ * members, replayed from a CUDA graph of up to 64 steps.  Every ensemble
+ * call returns LBM_ERR_STATE (with lbm_ensemble_last_error) when a member
+ * was stepped, re-initialised, given a new geometry or nodes, or switched
+ * to another scheme or layout outside the ensemble since its tables were
+ * built, or when a member handle is poisoned; create a new ensemble then. */
 lbm_status lbm_ensemble_step(lbm_ensemble* e, int64_t nsteps);
 /* Same result, member by member (two launches per member per step: the
  * baseline). */
