@@ -126,7 +126,11 @@ lbm_status lbm_destroy(lbm_handle* h);
  * component-major (ux[N], uy[N], uz[N]; wall velocity of MOVING cells, state
  * of EQ cells) or NULL (zero); node_rho: N floats (EQ density) or NULL (1).
  * The populations of cells that are solid in the new geometry are set to
- * zero.  With A-A streaming, OUTFLOW and FREESLIP cells give
+ * zero.  The first call with flags allocates, through the lattice's
+ * allocator, the flag bytes (N), a 32-bit wall mask per cell (4 N bytes:
+ * the directions whose upstream cell is solid, read by the fast kernels
+ * for cells that only bounce back), the node arrays the flags need and
+ * the list of boundary cells.  With A-A streaming, OUTFLOW and FREESLIP cells give
  * LBM_ERR_UNSUPPORTED.  Invalid bit combinations, and OUTFLOW cells whose
  * -x neighbour is solid (an outflow cell pulls as if it sat there), give
  * LBM_ERR_ARG. */
