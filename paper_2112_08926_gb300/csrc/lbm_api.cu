@@ -334,6 +334,7 @@ extern "C" lbm_status lbm_set_geometry(lbm_handle* h, const uint8_t* flags, cons
         h->special_cap = 0;
         h->n_special = h->n_complex = 0;
         h->release((void*&)h->flags, N);
+        h->release((void*&)h->walls, N * sizeof(uint32_t));
         h->release((void*&)h->node_u, 3 * N * sizeof(float));
         h->release((void*&)h->node_rho, N * sizeof(float));
         return ensure_layout(h);
