@@ -308,6 +308,12 @@ def test_chunked_lattice_takes_flags_later():
     g.step(3)
     o.step(3)
     assert np.array_equal(g.f(), o.f())
+    # flags again: the flag bytes and wall masks are allocated anew
+    g.set_geometry(*geo)
+    o.set_geometry(*geo)
+    g.step(4)
+    o.step(4)
+    assert np.array_equal(g.f(), o.f())
 
 
 # ---------------------------------------------------------------- no DDF shifting
