@@ -249,6 +249,7 @@ class Lattice:
         self.scheme = {0: "AB", 1: "AA"}[self.info().scheme]   # AUTO resolved at creation
 
     def close(self):
+        """Release the lattice's device memory (lbm_destroy); idempotent."""
         if self._h:
             self._L.lbm_destroy(self._h)
             self._h = None
@@ -261,12 +262,15 @@ class Lattice:
 
     @property
     def handle(self):
+        """The lbm_handle* of the C ABI."""
         return self._h
 
     def _c(self, status):
         _check(status, self._h)
 
     def set_geometry(self, flags=None, node_u=None, node_rho=None):
+        """Cell flags (N bytes, x fastest; None: fully periodic fluid), wall/EQ
+        velocities (3 x N floats) and EQ densities (N floats) (lbm_set_geometry)."""
         fl = None if flags is None else np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
         nu = None if node_u is None else np.ascontiguousarray(node_u, dtype=np.float32).reshape(-1)
         nr = None if node_rho is None else np.ascontiguousarray(node_rho, dtype=np.float32).reshape(-1)
@@ -303,6 +307,8 @@ class Lattice:
         return tuple(out)
 
     def set_rho_u(self, rho=None, ux=None, uy=None, uz=None):
+        """Equilibrium populations from host fields of N values each; None: rho
+        1, u 0 (lbm_set_rho_u)."""
         arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float64).reshape(-1)
                 for a in (rho, ux, uy, uz)]
         self._c(self._L.lbm_set_rho_u(self._h, *[_ptr(a) for a in arrs]))
@@ -313,11 +319,13 @@ class Lattice:
         self._c(self._L.lbm_set_rho_u(self._h, cv(rho), cv(ux), cv(uy), cv(uz)))
 
     def set_f(self, f):
+        """Populations f_i (not shifted), q x N doubles, slot-major (lbm_set_f)."""
         a = np.ascontiguousarray(f, dtype=np.float64).reshape(-1)
         assert a.size == self.q * self.N
         self._c(self._L.lbm_set_f(self._h, _ptr(a)))
 
     def step(self, n=1):
+        """Advance n stream-collide steps (lbm_step)."""
         self._c(self._L.lbm_step(self._h, int(n)))
 
     def set_divergence_check(self, every, mass_tol=0.0):
@@ -327,30 +335,36 @@ class Lattice:
         self._c(self._L.lbm_set_divergence_check(self._h, int(every), float(mass_tol)))
 
     def rho_u(self):
+        """(rho, ux, uy, uz) of every cell, each shaped (nz, ny, nx) (lbm_get_rho_u)."""
         out = [np.empty(self.N, dtype=np.float64) for _ in range(4)]
         self._c(self._L.lbm_get_rho_u(self._h, *[_ptr(a) for a in out]))
         return tuple(a.reshape(self.shape) for a in out)
 
     def get_rho_u_ptr(self, rho, ux, uy, uz):
+        """lbm_get_rho_u into host pointers (e.g. pinned tensors' data_ptr()) or None."""
         cv = lambda p: None if p is None else ctypes.c_void_p(p)
         self._c(self._L.lbm_get_rho_u(self._h, cv(rho), cv(ux), cv(uy), cv(uz)))
 
     def f(self):
+        """Streamed populations f_i (not shifted), shaped (q, nz, ny, nx) (lbm_get_f)."""
         out = np.empty(self.q * self.N, dtype=np.float64)
         self._c(self._L.lbm_get_f(self._h, _ptr(out)))
         return out.reshape((self.q,) + self.shape)
 
     def reduce(self):
+        """(mass, kinetic energy) as FP64 sums over the lattice (lbm_reduce)."""
         m, e = ctypes.c_double(), ctypes.c_double()
         self._c(self._L.lbm_reduce(self._h, ctypes.byref(m), ctypes.byref(e)))
         return m.value, e.value
 
     def info(self) -> lbm_info:
+        """Layout, variant, scheme, step count and device bytes (lbm_get_info)."""
         inf = lbm_info()
         self._c(self._L.lbm_get_info(self._h, ctypes.byref(inf)))
         return inf
 
     def set_block(self, bx, by):
+        """Thread-block shape of the kernels that take one (lbm_set_block)."""
         self._c(self._L.lbm_set_block(self._h, int(bx), int(by)))
 
     def autotune(self, trial_steps=20):
@@ -371,6 +385,7 @@ class Lattice:
         self._c(self._L.lbm_set_variant(self._h, VARIANTS[variant]))
 
     def variant(self) -> str:
+        """The kernel variant in use (lbm_get_variant)."""
         return {v: k for k, v in VARIANTS.items()}[self._L.lbm_get_variant(self._h)]
 
 
@@ -386,6 +401,8 @@ class Ensemble:
         _check(self._L.lbm_ensemble_create(arr, len(self.members), ctypes.byref(self._e)))
 
     def close(self):
+        """Free the ensemble's tables and return chunked members to their own
+        layout (lbm_ensemble_destroy); idempotent."""
         if self._e:
             self._L.lbm_ensemble_destroy(self._e)
             self._e = None
@@ -397,12 +414,15 @@ class Ensemble:
             pass
 
     def step(self, n=1):
+        """Advance every member n steps, one launch per step for all (lbm_ensemble_step)."""
         _check(self._L.lbm_ensemble_step(self._e, int(n)), self._e, ensemble=True)
 
     def step_each(self, n=1):
+        """The same steps as launches member by member (lbm_ensemble_step_each)."""
         _check(self._L.lbm_ensemble_step_each(self._e, int(n)), self._e, ensemble=True)
 
     def set_block(self, bx, by):
+        """Cells per tile of the per-cell kernel (by = 1; lbm_ensemble_set_block)."""
         _check(self._L.lbm_ensemble_set_block(self._e, int(bx), int(by)), self._e, ensemble=True)
 
     def set_variant(self, variant, warps=4):
@@ -412,6 +432,7 @@ class Ensemble:
         _check(self._L.lbm_ensemble_set_variant(self._e, code, int(warps)), self._e, ensemble=True)
 
     def variant(self) -> str:
+        """The ensemble kernel in use: 'per_cell' or 'paired'."""
         return {0: "per_cell", 1: "paired"}[self._L.lbm_ensemble_get_variant(self._e)]
 
     def set_layout(self, layout):
@@ -420,17 +441,20 @@ class Ensemble:
         _check(self._L.lbm_ensemble_set_layout(self._e, {"soa": 0, "chunked": 1}[layout]), self._e, ensemble=True)
 
     def layout(self) -> str:
+        """The members' population layout: 'soa' or 'chunked'."""
         return {0: "soa", 1: "chunked"}[self._L.lbm_ensemble_get_layout(self._e)]
 
     def autotune(self, trial_steps=5):
-        """Picks kernel, tile and streaming scheme; returns (cells per tile,
-        1 for the per-cell kernel or warps per tile of the paired one)."""
+        """Picks the member layout, the kernel, the tile and the streaming
+        scheme by timing (lbm_ensemble_autotune); returns (cells per tile, 1
+        for the per-cell kernel or warps per tile of the paired one)."""
         bx, by = ctypes.c_int(), ctypes.c_int()
         _check(self._L.lbm_ensemble_autotune(self._e, int(trial_steps), ctypes.byref(bx), ctypes.byref(by)),
                self._e, ensemble=True)
         return bx.value, by.value
 
     def scheme(self) -> str:
+        """The members' streaming scheme: 'AB' or 'AA' (lbm_ensemble_scheme)."""
         return {v: k for k, v in SCHEMES.items()}[self._L.lbm_ensemble_scheme(self._e)]
 
 
